@@ -1,0 +1,241 @@
+/*
+ * ot_assoc.h -- C ABI of the GB300 entropic-OT device-association library.
+ *
+ * Method: Paschos, Liakopoulos, Debbah, Wen, "Computational Optimal Transport
+ * for 5G Massive C-RAN Device Association" (arXiv 1805.01559).
+ *   Sec. II-A   downlink rate R_ij = W log2(1 + SINR_ji), all other RRHs interfere
+ *   Sec. II-B   RRH load rho_j = sum_i lambda_i pi_ij / (mu R_ij)
+ *   Sec. III-B  regularized OT, Eq. (5); Algorithm 1 (Sinkhorn)
+ *   Sec. IV     OT instance: C_ij = 1/(mu R_ij), p = lambda, q = RRH target; Lemma 1
+ *   Sec. V      Algorithm 2 (adaptive Sinkhorn association)
+ *
+ * Conventions (every entry point):
+ *   * i indexes devices (rows, I of them), j indexes RRHs (columns, J of them).
+ *     Matrices are row-major I x J with a leading dimension `ld` (elements between
+ *     the starts of consecutive rows; ld = 0 means ld = J).
+ *   * Pointers marked [device] are CUDA device pointers owned by the caller; the
+ *     library never frees or retains them past the call.  Pointers marked [host]
+ *     are ordinary host memory.  Scratch memory is owned by the context.
+ *   * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is stream-ordered.  Entry points that return host scalars synchronise
+ *     the stream before returning; the others only enqueue.
+ *   * Errors are returned as ot_status codes; nothing aborts, traps or throws.
+ *     On error the message is available from ot_assoc_last_error(ctx).
+ *   * Potentials: pi_ij = exp((f_i + g_j - C_ij) / eps) (Sec. III-B, KKT form
+ *     pi = xi e^{-alpha} e^{-beta}: f_i = -eps alpha_i, g_j = -eps beta_j, i.e.
+ *     a_i = exp(f_i/eps), b_j = exp(g_j/eps) of Algorithm 1).
+ *   * The marginals are each normalised by their own sum before iterating; they
+ *     must balance (Eqs. 3-4 force sum p = sum q) to 1e-5 relative.  Residuals and
+ *     `tol` refer to the unit-mass plan: err = sum_i |sum_j pi_ij - p_i| / sum p.
+ *   * Stopping rule ("while accuracy" of Algorithm 1, with the "total absolute
+ *     residual" of Sec. III-C): after each full iteration k (a-update then
+ *     b-update) the row residual of pi^(k) is compared with `tol`; the loop ends at
+ *     the first k with residual <= tol, or at k = max_iter (status
+ *     OT_NOT_CONVERGED, results still valid).
+ */
+#ifndef OT_ASSOC_H
+#define OT_ASSOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OT_OK = 0,
+    OT_NOT_CONVERGED = 1,  /* max_iter reached; f, g and the summary are valid */
+    OT_EINVAL = -1,        /* bad size, pointer, parameter or input value */
+    OT_ENOMEM = -2,        /* scratch would exceed the context's HBM budget, or cudaMalloc failed */
+    OT_ECUDA = -3,         /* a CUDA runtime call failed (message has the CUDA error) */
+    OT_ETIMEOUT = -4,      /* a bounded device-side wait gave up; the context stays usable */
+    OT_EBUSY = -5,         /* serving: no free slot / budget right now */
+    OT_EUNSUPPORTED = -6   /* shape outside the compiled kernel range (e.g. J > 8192) */
+} ot_status;
+
+typedef struct ot_assoc_ctx ot_assoc_ctx;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int ot_assoc_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* ot_assoc_status_string(int status);
+
+/*
+ * Create a context on CUDA device `device`.  The context owns all scratch
+ * memory; it never holds more than `hbm_budget_bytes` of it (0 = no limit other
+ * than the device).  Returns OT_EINVAL for a bad device, OT_ECUDA on a CUDA error.
+ * A context is not thread-safe: use one per host thread.  Its scratch is shared by
+ * all calls, so calls on different streams must not overlap in time.
+ */
+ot_status ot_assoc_create(ot_assoc_ctx** ctx, int device, size_t hbm_budget_bytes);
+
+/* Release the context and its scratch.  NULL is ignored. */
+void ot_assoc_destroy(ot_assoc_ctx* ctx);
+
+/* Last error message of this context ("" if none).  Valid until the next call. */
+const char* ot_assoc_last_error(const ot_assoc_ctx* ctx);
+
+/* Bytes of device scratch the context holds right now. */
+size_t ot_assoc_scratch_bytes(const ot_assoc_ctx* ctx);
+
+/*
+ * Set the iteration bound of every device-side spin wait (grid barriers and
+ * batch work queues).  A wait that exceeds it stops the kernel with
+ * OT_ETIMEOUT instead of hanging.  Default 1 << 24 polls (seconds).  Values < 1
+ * restore the default.
+ */
+void ot_assoc_set_spin_limit(ot_assoc_ctx* ctx, int64_t polls);
+
+/*
+ * Downlink rates, Sec. II-A:
+ *   SINR_ij = P_j G_ij / (sum_{k != j} P_k G_ik + N0),   R_ij = W_hz * log2(1 + SINR_ij).
+ * G   [device] float, I x J (ld_g, 0 = J): G[i*ld + j] = path gain RRH j -> device i, >= 0.
+ * P   [device] float, J: transmit powers, >= 0.
+ * R_out [device] float, I x J (ld_r, 0 = J).
+ * The interference sum is formed per row in FP64 (total minus own term); the
+ * rate uses log1p.  Enqueue only.  OT_EINVAL for I, J <= 0, N0 < 0, W_hz <= 0.
+ */
+ot_status ot_assoc_build_rates(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const float* P,
+                               int64_t I, int64_t J, double N0, double W_hz, float* R_out,
+                               int64_t ld_r, void* stream);
+
+/*
+ * Cost per unit traffic, Sec. IV choice (ii):  C_ij = 1 / (mu R_ij).
+ * R     [device] float, I x J (ld_r, 0 = J), every entry finite and > 0.
+ * C_out [device] float, I x J (ld_c, 0 = J).
+ * If eps_out != NULL, also *eps_out [host] = eps_rel * median(C), the median
+ * over all I*J entries of the FP32 C (mean of the two middle values when I*J is
+ * even); this synchronises the stream.  OT_EINVAL for a non-positive or
+ * non-finite R entry (checked on the device), mu <= 0, or eps_rel <= 0 with
+ * eps_out given.
+ */
+ot_status ot_assoc_build_cost(ot_assoc_ctx* ctx, const float* R, int64_t ld_r, int64_t I,
+                              int64_t J, double mu, float* C_out, int64_t ld_c, double eps_rel,
+                              double* eps_out, void* stream);
+
+/*
+ * Exact median of n floats (no NaN): the middle order statistic, or the mean of
+ * the two middle ones for even n.  x [device]; *median_out [host].  Synchronises.
+ */
+ot_status ot_assoc_median_f32(ot_assoc_ctx* ctx, const float* x, int64_t n, double* median_out,
+                              void* stream);
+
+/*
+ * maxSINR (strongest-signal) association, Sec. II-C and Lemma 1: device i picks
+ * j*(i) = argmax_j R_ij (lowest j on ties).
+ * R        [device] float I x J (ld_r, 0 = J);  traffic [device] float, I.
+ * assoc_out  [device] int32, I (may be NULL).
+ * Lambda_out [device] double, J: Lambda_j = sum_{i: j*(i)=j} traffic_i (may be NULL).
+ * *total_load_out [host] (may be NULL; synchronises): sum_i traffic_i / (mu R_{i j*(i)}).
+ */
+ot_status ot_assoc_maxsinr(ot_assoc_ctx* ctx, const float* R, int64_t ld_r, const float* traffic,
+                           int64_t I, int64_t J, double mu, int32_t* assoc_out,
+                           double* Lambda_out, double* total_load_out, void* stream);
+
+/* Outputs of a solve.  Device pointers are caller-owned; NULL = do not produce. */
+typedef struct {
+    float* pi;             /* [device] I x J plan (mass units of the caller's p), ld = pi_ld */
+    int64_t pi_ld;         /* 0 = J */
+    double* f;             /* [device] I: potentials f_i (required) */
+    double* g;             /* [device] J: potentials g_j (required; read first when warm_start) */
+    double* rrh_load;      /* [device] J: rho_j = sum_i C_ij pi_ij (Sec. II-B with x = pi) */
+    double transport_cost; /* [host-filled] sum_ij C_ij pi_ij (objective of Eq. 2) */
+    double marg_err_row;   /* [host-filled] sum_i |sum_j pi_ij - p_i| / sum p, FP64 reduction */
+    double marg_err_col;   /* [host-filled] sum_j |sum_i pi_ij - q_j| / sum p, FP64 reduction */
+    int32_t iters;         /* [host-filled] completed Sinkhorn iterations k */
+    int32_t status;        /* [host-filled] same as the return value */
+    int32_t absorptions;   /* [host-filled] kernel rebuilds (stored-kernel forms; 0 otherwise) */
+    int32_t reserved;
+} ot_assoc_result;
+
+/*
+ * Algorithm 1 on the OT instance of Sec. IV: builds C = 1/(mu R) into context
+ * scratch, then solves Eq. (5) in the log domain with FP32 per-cell arithmetic.
+ * R             [device] float I x J (ld_r, 0 = J), finite and > 0.
+ * traffic       [device] float I: p = lambda (> 0).
+ * rrh_marginal  [device] float J: q (> 0), sum q = sum p.
+ * eps > 0 (absolute), tol >= 0, max_iter >= 1.  warm_start != 0 starts from
+ * b = exp(out->g / eps) instead of b = 1 (Algorithm 1's initialisation).
+ * Synchronises the stream (the summary scalars are host-filled).  Returns
+ * OT_OK, OT_NOT_CONVERGED, or an error (then `out` is unspecified).
+ */
+ot_status ot_assoc_solve(ot_assoc_ctx* ctx, const float* R, int64_t ld_r, const float* traffic,
+                         const float* rrh_marginal, int64_t I, int64_t J, double mu, double eps,
+                         double tol, int32_t max_iter, int32_t warm_start, ot_assoc_result* out,
+                         void* stream);
+
+/*
+ * Same as ot_assoc_solve for a caller-built cost matrix (Eq. 5 with any finite C;
+ * +inf entries mean "no link", but every row and column needs a finite entry).
+ * C [device] float I x J with ld_c (0 = J).  A C whose ld_c is a multiple of 4
+ * and whose base is 16-byte aligned is read in place, in 16-byte chunks (so the
+ * allocation must extend to the end of the last row's final 16-byte chunk);
+ * otherwise it is first copied into aligned scratch.
+ */
+ot_status ot_assoc_solve_cost(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* p,
+                              const float* q, int64_t I, int64_t J, double eps, double tol,
+                              int32_t max_iter, int32_t warm_start, ot_assoc_result* out,
+                              void* stream);
+
+/*
+ * FP64 variant of ot_assoc_solve_cost (all per-cell arithmetic in double).
+ * C [device] double I x J (ld_c, 0 = J); p [device] double I; q [device] double J.
+ * out->pi, if given, is still float.
+ */
+ot_status ot_assoc_solve_f64(ot_assoc_ctx* ctx, const double* C, int64_t ld_c, const double* p,
+                             const double* q, int64_t I, int64_t J, double eps, double tol,
+                             int32_t max_iter, int32_t warm_start, ot_assoc_result* out,
+                             void* stream);
+
+/*
+ * Device timings of the last solve on this context (CUDA events recorded on the
+ * solve's stream around each phase; only while timing is enabled).
+ */
+typedef struct {
+    double init_ms;      /* marginal sums + iteration 1 (exact log-domain step) */
+    double loop_ms;      /* persistent kernel: iterations 2.. (one read of C per sweep) */
+    double finalize_ms;  /* plan, potentials, FP64 reductions */
+    int32_t sweeps;      /* full reads of the cost/kernel matrix made by the persistent kernel */
+    int32_t valid;       /* 1 when the fields above belong to the last solve */
+} ot_assoc_timings;
+
+/* Turn phase timing on (1) or off (0).  Off by default; costs a few events per solve. */
+void ot_assoc_enable_timing(ot_assoc_ctx* ctx, int on);
+
+/* Timings of the last solve (valid = 0 if timing was off or the solve failed). */
+ot_status ot_assoc_last_timings(const ot_assoc_ctx* ctx, ot_assoc_timings* out);
+
+/* Number of CUDA kernels this context has launched so far (all entry points). */
+uint64_t ot_assoc_launch_count(const ot_assoc_ctx* ctx);
+
+/* Storage of the Gibbs kernel in the stored-kernel (scaling-domain) form. */
+typedef enum {
+    OT_KERNEL_F32 = 0,
+    OT_KERNEL_BF16 = 1,
+    OT_KERNEL_F16 = 2
+} ot_kernel_format;
+
+/*
+ * Stored-kernel form of Algorithm 1 (the a/b scaling iteration as printed) with
+ * absorption: K~_ij = exp((fh_i + gh_j - C_ij)/eps) is kept in `format`
+ * (each row scaled so its largest entry is 1), the scalings a, b are FP32, and
+ * whenever a scaling leaves [2^-absorb_log2, 2^absorb_log2] relative to its
+ * value at the last rebuild it is folded into (fh, gh) and K~ is rebuilt from C
+ * (absorb_log2 <= 0 selects the format's default).  Accumulation is FP32; the
+ * final summary uses FP64 reductions.  The first iteration runs in the log
+ * domain from C so that no column can underflow.
+ * C [device] float I x J (ld_c, 0 = J), kept for rebuilds; other arguments as
+ * ot_assoc_solve_cost.
+ */
+ot_status ot_assoc_solve_lowp(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* p,
+                              const float* q, int64_t I, int64_t J, double eps, double tol,
+                              int32_t max_iter, int32_t warm_start, int32_t format,
+                              double absorb_log2, ot_assoc_result* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OT_ASSOC_H */

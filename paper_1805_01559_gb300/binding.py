@@ -1,0 +1,344 @@
+"""Thin ctypes binding of libot_assoc.so (include/ot_assoc.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream.  There is no CPU
+fallback: if the library cannot be loaded, importing ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+OT_OK = 0
+OT_NOT_CONVERGED = 1
+OT_EINVAL = -1
+OT_ENOMEM = -2
+OT_ECUDA = -3
+OT_ETIMEOUT = -4
+OT_EBUSY = -5
+OT_EUNSUPPORTED = -6
+
+OT_KERNEL_F32 = 0
+OT_KERNEL_BF16 = 1
+OT_KERNEL_F16 = 2
+
+_lib = None
+
+
+class OTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+def _status_name(s: int) -> str:
+    return {0: "OT_OK", 1: "OT_NOT_CONVERGED", -1: "OT_EINVAL", -2: "OT_ENOMEM", -3: "OT_ECUDA",
+            -4: "OT_ETIMEOUT", -5: "OT_EBUSY", -6: "OT_EUNSUPPORTED"}.get(s, f"status {s}")
+
+
+class ot_assoc_result(ctypes.Structure):
+    _fields_ = [
+        ("pi", ctypes.c_void_p),
+        ("pi_ld", ctypes.c_int64),
+        ("f", ctypes.c_void_p),
+        ("g", ctypes.c_void_p),
+        ("rrh_load", ctypes.c_void_p),
+        ("transport_cost", ctypes.c_double),
+        ("marg_err_row", ctypes.c_double),
+        ("marg_err_col", ctypes.c_double),
+        ("iters", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("absorptions", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class ot_assoc_timings(ctypes.Structure):
+    _fields_ = [
+        ("init_ms", ctypes.c_double),
+        ("loop_ms", ctypes.c_double),
+        ("finalize_ms", ctypes.c_double),
+        ("sweeps", ctypes.c_int32),
+        ("valid", ctypes.c_int32),
+    ]
+
+
+# (name, restype, argtypes) of every exported entry point in include/ot_assoc.h
+_VP, _I64, _I32, _D, _SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
+_PD = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "ot_assoc_version": (ctypes.c_int, []),
+    "ot_assoc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ot_assoc_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _SZ]),
+    "ot_assoc_destroy": (None, [_VP]),
+    "ot_assoc_last_error": (ctypes.c_char_p, [_VP]),
+    "ot_assoc_scratch_bytes": (_SZ, [_VP]),
+    "ot_assoc_set_spin_limit": (None, [_VP, _I64]),
+    "ot_assoc_enable_timing": (None, [_VP, ctypes.c_int]),
+    "ot_assoc_last_timings": (ctypes.c_int, [_VP, ctypes.POINTER(ot_assoc_timings)]),
+    "ot_assoc_launch_count": (ctypes.c_uint64, [_VP]),
+    "ot_assoc_build_rates": (ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _I64, _D, _D, _VP, _I64, _VP]),
+    "ot_assoc_build_cost": (ctypes.c_int, [_VP, _VP, _I64, _I64, _I64, _D, _VP, _I64, _D, _PD, _VP]),
+    "ot_assoc_median_f32": (ctypes.c_int, [_VP, _VP, _I64, _PD, _VP]),
+    "ot_assoc_maxsinr": (ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _I64, _D, _VP, _VP, _PD, _VP]),
+    "ot_assoc_solve": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _D, _I32, _I32,
+                                      ctypes.POINTER(ot_assoc_result), _VP]),
+    "ot_assoc_solve_cost": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,
+                                           ctypes.POINTER(ot_assoc_result), _VP]),
+    "ot_assoc_solve_f64": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,
+                                          ctypes.POINTER(ot_assoc_result), _VP]),
+    "ot_assoc_solve_lowp": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,
+                                           _I32, _D, ctypes.POINTER(ot_assoc_result), _VP]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libot_assoc.so (building it first if asked).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"{path} is missing: run paper_1805_01559_gb300.build.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, name: str, dims: int):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.dim() != dims:
+        raise ValueError(f"{name} must have {dims} dims")
+    if dims == 2:
+        if t.stride(1) != 1:
+            raise ValueError(f"{name} must be row-major with unit column stride")
+    elif not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+@dataclasses.dataclass
+class Result:
+    f: torch.Tensor
+    g: torch.Tensor
+    pi: Optional[torch.Tensor]
+    rrh_load: Optional[torch.Tensor]
+    transport_cost: float
+    marg_err_row: float
+    marg_err_col: float
+    iters: int
+    status: int
+    absorptions: int
+
+    @property
+    def converged(self) -> bool:
+        return self.status == OT_OK
+
+
+class Context:
+    """One library context (scratch arena) on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self._L = lib()
+        h = ctypes.c_void_p()
+        st = self._L.ot_assoc_create(ctypes.byref(h), int(device), int(hbm_budget_bytes))
+        if st != OT_OK:
+            raise OTError(st, "ot_assoc_create failed")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ot_assoc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def last_error(self) -> str:
+        return self._L.ot_assoc_last_error(self._h).decode()
+
+    def scratch_bytes(self) -> int:
+        return int(self._L.ot_assoc_scratch_bytes(self._h))
+
+    def set_spin_limit(self, polls: int) -> None:
+        self._L.ot_assoc_set_spin_limit(self._h, int(polls))
+
+    def enable_timing(self, on: bool = True) -> None:
+        self._L.ot_assoc_enable_timing(self._h, 1 if on else 0)
+
+    def last_timings(self) -> dict:
+        t = ot_assoc_timings()
+        self._L.ot_assoc_last_timings(self._h, ctypes.byref(t))
+        return {"init_ms": t.init_ms, "loop_ms": t.loop_ms, "finalize_ms": t.finalize_ms,
+                "sweeps": t.sweeps, "valid": bool(t.valid)}
+
+    def launch_count(self) -> int:
+        return int(self._L.ot_assoc_launch_count(self._h))
+
+    def _check(self, st: int, allow_nc: bool = False) -> int:
+        if st == OT_OK or (allow_nc and st == OT_NOT_CONVERGED):
+            return st
+        raise OTError(st, self.last_error())
+
+    # ---- cost construction --------------------------------------------------------------
+    def build_rates(self, G: torch.Tensor, P: torch.Tensor, N0: float, W_hz: float,
+                    R_out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        _need(G, torch.float32, "G", 2)
+        _need(P, torch.float32, "P", 1)
+        I, J = G.shape
+        if R_out is None:
+            R_out = torch.empty((I, J), dtype=torch.float32, device=G.device)
+        self._check(self._L.ot_assoc_build_rates(self._h, _ptr(G), G.stride(0), _ptr(P), I, J, float(N0),
+                                                 float(W_hz), _ptr(R_out), R_out.stride(0), _stream(stream)))
+        return R_out
+
+    def build_cost(self, R: torch.Tensor, mu: float, eps_rel: Optional[float] = None,
+                   C_out: Optional[torch.Tensor] = None, stream=None):
+        _need(R, torch.float32, "R", 2)
+        I, J = R.shape
+        if C_out is None:
+            C_out = torch.empty((I, J), dtype=torch.float32, device=R.device)
+        eps = ctypes.c_double(0.0)
+        self._check(self._L.ot_assoc_build_cost(self._h, _ptr(R), R.stride(0), I, J, float(mu), _ptr(C_out),
+                                                C_out.stride(0), float(eps_rel or 0.0),
+                                                ctypes.byref(eps) if eps_rel is not None else None,
+                                                _stream(stream)))
+        return C_out, (eps.value if eps_rel is not None else None)
+
+    def median_f32(self, x: torch.Tensor, stream=None) -> float:
+        _need(x, torch.float32, "x", 1)
+        out = ctypes.c_double(0.0)
+        self._check(self._L.ot_assoc_median_f32(self._h, _ptr(x), x.numel(), ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def maxsinr(self, R: torch.Tensor, traffic: torch.Tensor, mu: float, stream=None):
+        _need(R, torch.float32, "R", 2)
+        _need(traffic, torch.float32, "traffic", 1)
+        I, J = R.shape
+        assoc = torch.empty(I, dtype=torch.int32, device=R.device)
+        Lam = torch.empty(J, dtype=torch.float64, device=R.device)
+        tot = ctypes.c_double(0.0)
+        self._check(self._L.ot_assoc_maxsinr(self._h, _ptr(R), R.stride(0), _ptr(traffic), I, J, float(mu),
+                                             _ptr(assoc), _ptr(Lam), ctypes.byref(tot), _stream(stream)))
+        return assoc, Lam, tot.value
+
+    # ---- solves -------------------------------------------------------------------------
+    def _result(self, I, J, device, want_pi, want_load, f, g):
+        f = torch.empty(I, dtype=torch.float64, device=device) if f is None else f
+        g = torch.empty(J, dtype=torch.float64, device=device) if g is None else g
+        pi = torch.empty((I, J), dtype=torch.float32, device=device) if want_pi else None
+        load = torch.empty(J, dtype=torch.float64, device=device) if want_load else None
+        r = ot_assoc_result()
+        r.pi = pi.data_ptr() if pi is not None else None
+        r.pi_ld = J
+        r.f = f.data_ptr()
+        r.g = g.data_ptr()
+        r.rrh_load = load.data_ptr() if load is not None else None
+        return r, f, g, pi, load
+
+    @staticmethod
+    def _pack(r, f, g, pi, load) -> Result:
+        return Result(f=f, g=g, pi=pi, rrh_load=load, transport_cost=r.transport_cost,
+                      marg_err_row=r.marg_err_row, marg_err_col=r.marg_err_col, iters=r.iters,
+                      status=r.status, absorptions=r.absorptions)
+
+    def solve(self, R, traffic, rrh_marginal, mu, eps, tol=1e-6, max_iter=2000, warm_g=None,
+              want_pi=False, want_load=True, f=None, g=None, stream=None) -> Result:
+        """Algorithm 1 on C = 1/(mu R) (FP32 log domain).  warm_g: start from b = exp(g/eps)."""
+        _need(R, torch.float32, "R", 2)
+        _need(traffic, torch.float32, "traffic", 1)
+        _need(rrh_marginal, torch.float32, "rrh_marginal", 1)
+        I, J = R.shape
+        if warm_g is not None:
+            g = warm_g if g is None else g.copy_(warm_g)
+        r, f, g, pi, load = self._result(I, J, R.device, want_pi, want_load, f, g)
+        st = self._L.ot_assoc_solve(self._h, _ptr(R), R.stride(0), _ptr(traffic), _ptr(rrh_marginal), I, J,
+                                    float(mu), float(eps), float(tol), int(max_iter), int(warm_g is not None),
+                                    ctypes.byref(r), _stream(stream))
+        self._check(st, allow_nc=True)
+        return self._pack(r, f, g, pi, load)
+
+    def solve_cost(self, C, p, q, eps, tol=1e-6, max_iter=2000, warm_g=None, want_pi=False,
+                   want_load=True, f=None, g=None, stream=None) -> Result:
+        _need(C, torch.float32, "C", 2)
+        _need(p, torch.float32, "p", 1)
+        _need(q, torch.float32, "q", 1)
+        I, J = C.shape
+        if warm_g is not None:
+            g = warm_g if g is None else g.copy_(warm_g)
+        r, f, g, pi, load = self._result(I, J, C.device, want_pi, want_load, f, g)
+        st = self._L.ot_assoc_solve_cost(self._h, _ptr(C), C.stride(0), _ptr(p), _ptr(q), I, J, float(eps),
+                                         float(tol), int(max_iter), int(warm_g is not None), ctypes.byref(r),
+                                         _stream(stream))
+        self._check(st, allow_nc=True)
+        return self._pack(r, f, g, pi, load)
+
+    def solve_f64(self, C, p, q, eps, tol=1e-6, max_iter=2000, warm_g=None, want_pi=False,
+                  want_load=True, stream=None) -> Result:
+        _need(C, torch.float64, "C", 2)
+        _need(p, torch.float64, "p", 1)
+        _need(q, torch.float64, "q", 1)
+        I, J = C.shape
+        g = warm_g.clone() if warm_g is not None else None
+        r, f, g, pi, load = self._result(I, J, C.device, want_pi, want_load, None, g)
+        st = self._L.ot_assoc_solve_f64(self._h, _ptr(C), C.stride(0), _ptr(p), _ptr(q), I, J, float(eps),
+                                        float(tol), int(max_iter), int(warm_g is not None), ctypes.byref(r),
+                                        _stream(stream))
+        self._check(st, allow_nc=True)
+        return self._pack(r, f, g, pi, load)
+
+    def solve_lowp(self, C, p, q, eps, tol=1e-3, max_iter=2000, fmt=OT_KERNEL_BF16, absorb_log2=0.0,
+                   warm_g=None, want_pi=False, want_load=True, stream=None) -> Result:
+        _need(C, torch.float32, "C", 2)
+        _need(p, torch.float32, "p", 1)
+        _need(q, torch.float32, "q", 1)
+        I, J = C.shape
+        g = warm_g.clone() if warm_g is not None else None
+        r, f, g, pi, load = self._result(I, J, C.device, want_pi, want_load, None, g)
+        st = self._L.ot_assoc_solve_lowp(self._h, _ptr(C), C.stride(0), _ptr(p), _ptr(q), I, J, float(eps),
+                                         float(tol), int(max_iter), int(warm_g is not None), int(fmt),
+                                         float(absorb_log2), ctypes.byref(r), _stream(stream))
+        self._check(st, allow_nc=True)
+        return self._pack(r, f, g, pi, load)
