@@ -180,6 +180,34 @@ ot_status ot_assoc_solve_cost(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, c
                               void* stream);
 
 /*
+ * ot_assoc_solve_cost without any memory allocation (the paper has no counterpart: this
+ * is a service of the library, not a step of the method).
+ *
+ * For callers that cannot allocate device memory when they solve: for example a radio
+ * scheduler that re-associates devices every few milliseconds and must not stall on
+ * cudaMalloc/cudaFree (which may synchronise the device and take unbounded time), or a
+ * process confined to a fixed memory pool.  It takes no context: all scratch lives in one
+ * file-scope device array of 8 MiB that is part of the library image, so every GPU that
+ * loads the library holds those 8 MiB until the process exits.  Nothing is allocated,
+ * freed, or taken from PyTorch's allocator; no event or pinned buffer is created.
+ *
+ * Limits: I <= 131072 devices, J <= 1024 RRHs (OT_EUNSUPPORTED beyond), C read in place,
+ * so ld_c must be a multiple of 4 and C 16-byte aligned (OT_EINVAL otherwise).  Same
+ * arguments, outputs, stopping rule and status codes as ot_assoc_solve_cost; error
+ * messages are not recorded (there is no context), only the status code.
+ *
+ * The first call on a device looks up the array's device address with that device
+ * current (cudaGetSymbolAddress), once; make that first call before any stream capture.
+ * Every call on a device shares the one array and overwrites what the previous call left
+ * there (the state words are cleared at the start of each call): calls whose GPU work
+ * overlaps -- on different streams or from different threads -- race and give wrong
+ * results.  Synchronises the stream before returning.
+ */
+ot_status ot_assoc_solve_cost_noalloc(const float* C, int64_t ld_c, const float* p, const float* q,
+                                      int64_t I, int64_t J, double eps, double tol, int32_t max_iter,
+                                      int32_t warm_start, ot_assoc_result* out, void* stream);
+
+/*
  * FP64 variant of ot_assoc_solve_cost (all per-cell arithmetic in double).
  * C [device] double I x J (ld_c, 0 = J); p [device] double I; q [device] double J.
  * out->pi, if given, is still float.

@@ -91,6 +91,8 @@ SIGNATURES = {
                                       ctypes.POINTER(ot_assoc_result), _VP]),
     "ot_assoc_solve_cost": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,
                                            ctypes.POINTER(ot_assoc_result), _VP]),
+    "ot_assoc_solve_cost_noalloc": (ctypes.c_int, [_VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,
+                                                   ctypes.POINTER(ot_assoc_result), _VP]),
     "ot_assoc_solve_f64": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,
                                           ctypes.POINTER(ot_assoc_result), _VP]),
     "ot_assoc_solve_lowp": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,

@@ -24,6 +24,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
+#include <mutex>
 
 #include "ot_common.cuh"
 #include "ot_internal.h"
@@ -721,3 +723,227 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
 }
 
 }  // namespace ota
+
+// ------------------------------------------------------------------------------------------
+// Solve without any allocation: the same kernels as launch_solve_f32, with every scratch
+// buffer carved out of one file-scope device array instead of context memory.
+//
+// Who needs it: callers that must not call cudaMalloc/cudaFree at solve time -- a radio
+// scheduler that re-associates devices every few milliseconds and cannot afford the device
+// synchronisation or unbounded latency those calls can bring, or a host process that runs
+// under a fixed memory pool and has no room to grow one.  The array is part of the loaded
+// library image: every GPU that loads the library holds NOALLOC_BYTES of it until exit.
+// ------------------------------------------------------------------------------------------
+namespace ota {
+
+static constexpr size_t NOALLOC_BYTES = size_t(8) << 20;  // 8 MiB
+static constexpr int64_t NOALLOC_MAX_I = 131072;
+static constexpr int NOALLOC_MAX_J = 1024;
+static constexpr int NOALLOC_MAX_CTAS = 320;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Byte offsets inside g_noalloc_scratch (all multiples of 256).
+static constexpr size_t NA_STATE = 0;                                    // DevScalars/LoopState/summary
+static constexpr size_t NA_COLERR = 4096;                                // Jp doubles
+static constexpr size_t NA_G = NA_COLERR + 8 * NOALLOC_MAX_J;            // Jp doubles
+static constexpr size_t NA_ERRPART = NA_G + 8 * NOALLOC_MAX_J;           // 2 * CTAs doubles
+static constexpr size_t NA_COLPART = NA_ERRPART + 16 * NOALLOC_MAX_CTAS; // CTAs * Jp double2
+static constexpr size_t NA_F = NA_COLPART + 16 * (size_t)NOALLOC_MAX_CTAS * NOALLOC_MAX_J;
+static constexpr size_t NA_END = NA_F + 16 * (size_t)NOALLOC_MAX_I;      // 2 * I doubles
+static_assert(NA_END <= NOALLOC_BYTES, "no-allocation scratch layout does not fit");
+static_assert(NA_COLPART % 256 == 0 && NA_F % 256 == 0, "alignment");
+
+// Device address of g_noalloc_scratch per device, looked up once with that device current.
+static std::mutex g_noalloc_mu;
+static unsigned char* g_noalloc_ptr[128];
+
+static ot_status noalloc_base(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= 128) return OT_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return OT_ECUDA;
+        }
+        g_noalloc_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return OT_OK;
+}
+
+static ot_status noalloc_solve(const SolveArgs& a, SolveSummary* sum_host) {
+    const int J = a.J;
+    const int64_t I = a.I;
+    const int Jp = (int)round_up(J, 4);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return OT_ECUDA;
+    }
+    unsigned char* base = nullptr;
+    ot_status st = noalloc_base(dev, &base);
+    if (st) return st;
+    Kernels kk;
+    const void* kfin = pick_finalize(J);
+    if (!pick_kernels(J, &kk) || !kfin) return OT_EUNSUPPORTED;
+    const int nteams = NT / (32 * kk.tw);
+    const size_t smem_loop = (size_t)nteams * Jp * sizeof(float);
+    const size_t smem_init = (size_t)nteams * Jp * sizeof(float2);
+    cudaError_t e;
+    for (const void* fn : {kk.loop, kk.init_rows}) {
+        const size_t sm = fn == kk.loop ? smem_loop : smem_init;
+        if (sm > 48 * 1024 &&
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+            cudaGetLastError();
+            return OT_ECUDA;
+        }
+    }
+    int occ = 0, occ_i = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk.loop, NT, smem_loop) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_i, kk.init_rows, NT, smem_init) != cudaSuccess) {
+        cudaGetLastError();
+        return OT_ECUDA;
+    }
+    if (occ < 1) return OT_EUNSUPPORTED;
+    const int64_t cap = NOALLOC_MAX_CTAS;
+    const int64_t want = (I + (int64_t)nteams * 8 - 1) / ((int64_t)nteams * 8);
+    const int nb_loop = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)occ * nsm, cap}));
+    const int nb_init = (int)std::max<int64_t>(
+        1, std::min<int64_t>({(I + nteams - 1) / nteams, (int64_t)std::max(occ_i, 1) * nsm, cap}));
+    const int nb_fin = (int)std::max<int64_t>(1, std::min<int64_t>({I, (int64_t)4 * nsm, cap}));
+
+    char* state = (char*)(base + NA_STATE);
+    DevScalars* sc = (DevScalars*)state;
+    LoopState* ls = (LoopState*)(state + 256);
+    SolveSummary* summ = (SolveSummary*)(state + 512);
+    double* colerr = (double*)(base + NA_COLERR);
+    double* G = (double*)(base + NA_G);
+    double* errpart = (double*)(base + NA_ERRPART);
+    void* colpart = (void*)(base + NA_COLPART);
+    double* F = (double*)(base + NA_F);
+
+    const double k = LOG2E / a.eps;
+    float k_hi, k_lo;
+    split_k(k, &k_hi, &k_lo);
+    cudaStream_t s = a.stream;
+    // The state words must start at zero on every call (the array keeps the last call's data).
+    e = cudaMemsetAsync(state, 0, 1024, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return OT_ECUDA;
+    }
+    sk_prep<<<1, 1024, 0, s>>>(a.p, a.q, I, J, a.warm_start ? a.out->g : nullptr, k, nullptr, sc, G);
+    {
+        double* F1 = F + I;
+        void* args[] = {(void*)&a.C, (void*)&a.ld, (void*)&I,    (void*)&J,  (void*)&Jp,   (void*)&a.p,
+                        (void*)&sc,  (void*)&G,    (void*)&F1,   &colpart,   (void*)&k_hi, (void*)&k_lo};
+        e = cudaLaunchKernel(kk.init_rows, dim3(nb_init), dim3(NT), args, smem_init, s);
+    }
+    if (e == cudaSuccess) {
+        sk_init_cols<<<(J + 7) / 8, 256, 0, s>>>((const float2*)colpart, nb_init, Jp, J, a.q, sc, G);
+        LoopParams P;
+        P.C = a.C;
+        P.ld = a.ld;
+        P.I = I;
+        P.J = J;
+        P.Jp = Jp;
+        P.p = a.p;
+        P.q = a.q;
+        P.sc = sc;
+        P.F0 = F;
+        P.F1 = F + I;
+        P.G = G;
+        P.colpart = (float*)colpart;
+        P.errpart = errpart;
+        P.st = ls;
+        P.k_hi = k_hi;
+        P.k_lo = k_lo;
+        P.tol = a.tol;
+        P.max_iter = a.max_iter;
+        P.spin = 1LL << 24;
+        void* args[] = {&P};
+        e = cudaLaunchCooperativeKernel(kk.loop, dim3(nb_loop), dim3(NT), args, smem_loop, s);
+    }
+    if (e == cudaSuccess) {
+        FinParams Q;
+        Q.C = a.C;
+        Q.ld = a.ld;
+        Q.I = I;
+        Q.J = J;
+        Q.Jp = Jp;
+        Q.p = a.p;
+        Q.sc = sc;
+        Q.F0 = F;
+        Q.F1 = F + I;
+        Q.st = ls;
+        Q.G = G;
+        Q.k_hi = k_hi;
+        Q.k_lo = k_lo;
+        Q.eps_ln2 = a.eps * LN2;
+        Q.pi = a.out->pi;
+        Q.pi_ld = a.out->pi_ld > 0 ? a.out->pi_ld : J;
+        Q.f_out = a.out->f;
+        Q.fpart = (double2*)colpart;
+        Q.epart = errpart;
+        void* args[] = {&Q};
+        e = cudaLaunchKernel(kfin, dim3(nb_fin), dim3(NT_F), args, 0, s);
+    }
+    if (e == cudaSuccess) {
+        sk_finalize_cols<<<(J + 15) / 16, 512, 0, s>>>((const double2*)colpart, nb_fin, Jp, J, a.q, sc, ls, G,
+                                                       a.eps * LN2, a.out->g, a.out->rrh_load, colerr);
+        sk_summary<<<1, 256, 0, s>>>(errpart, nb_fin, colerr, J, sc, ls, summ);
+        e = cudaMemcpyAsync(sum_host, summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return OT_ECUDA;
+    }
+    return OT_OK;
+}
+
+}  // namespace ota
+
+extern "C" ot_status ot_assoc_solve_cost_noalloc(const float* C, int64_t ld_c, const float* p, const float* q,
+                                                 int64_t I, int64_t J, double eps, double tol, int32_t max_iter,
+                                                 int32_t warm_start, ot_assoc_result* out, void* stream) {
+    using namespace ota;
+    if (!C || !p || !q || !out || !out->f || !out->g) return OT_EINVAL;
+    if (I <= 0 || J <= 0) return OT_EINVAL;
+    if (I > NOALLOC_MAX_I || J > NOALLOC_MAX_J) return OT_EUNSUPPORTED;
+    if (ld_c == 0) ld_c = J;
+    if (ld_c < J || ld_c % 4 != 0 || ((uintptr_t)C & 15u)) return OT_EINVAL;
+    if (!(eps > 0.0) || !std::isfinite(eps) || !(tol >= 0.0) || max_iter < 1) return OT_EINVAL;
+    if (out->pi && out->pi_ld != 0 && out->pi_ld < J) return OT_EINVAL;
+    SolveArgs a;
+    a.C = C;
+    a.ld = ld_c;
+    a.p = p;
+    a.q = q;
+    a.I = I;
+    a.J = (int)J;
+    a.eps = eps;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.warm_start = warm_start;
+    a.out = out;
+    a.stream = (cudaStream_t)stream;
+    SolveSummary sum;
+    ot_status st = noalloc_solve(a, &sum);
+    if (st) return st;
+    out->transport_cost = sum.cost;
+    out->marg_err_row = sum.err_row;
+    out->marg_err_col = sum.err_col;
+    out->iters = sum.iters;
+    out->absorptions = 0;
+    if (sum.status == DEV_EINVAL || sum.status == DEV_ENUMERIC) st = OT_EINVAL;
+    else if (sum.status == DEV_ETIMEOUT) st = OT_ETIMEOUT;
+    else if (sum.status != DEV_OK) st = OT_ECUDA;
+    else st = sum.converged ? OT_OK : OT_NOT_CONVERGED;
+    out->status = st;
+    return st;
+}
