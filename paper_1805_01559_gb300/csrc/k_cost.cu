@@ -27,17 +27,17 @@ static constexpr int NTC = 256;
 // ------------------------------------------------------------------------------------------
 // Rates: SINR_ij = P_j G_ij / (T_i - P_j G_ij), T_i = N0 + sum_k P_k G_ik,
 //        R_ij = W log2(1 + SINR_ij).
-// The row total is a compensated (Neumaier) FP32 sum per thread, combined in FP64, then
-// split into hi + lo floats.  Each own term P_j G_ij is kept as an exact hi + lo pair, so
+// The row total is a compensated (Neumaier) FP32 sum per thread, combined across threads
+// as error-free FP32 pairs (no FP64: GB300 issues it at a small fraction of the FP32 rate).  Each own term P_j G_ij is kept as an exact hi + lo pair, so
 // T_i - own loses nothing when one RRH dominates (T_hi - own_hi is exact by Sterbenz).
 // ------------------------------------------------------------------------------------------
 template <int TW, int VPT>
 __global__ void __launch_bounds__(NTC) k_rates(const float* __restrict__ G, int64_t ld_g,
                                                const float* __restrict__ P, int64_t I, int J,
-                                               double N0, float w_log2e, float* __restrict__ R,
+                                               float2 N0, float w_log2e, float* __restrict__ R,
                                                int64_t ld_r, int vec_out) {
     constexpr int TT = 32 * TW, NTEAMS = NTC / TT;
-    __shared__ double red[2 * NTEAMS * TW];
+    __shared__ float2 red[2 * NTEAMS * TW];
     const Team<TW> tm;
     float4 pw[VPT];
 #pragma unroll
@@ -66,9 +66,19 @@ __global__ void __launch_bounds__(NTC) k_rates(const float* __restrict__ G, int6
                 cmp += comp(lo[v], c);
                 s = t;
             }
-        const double T = team_reduce<TW, double, false>((double)s + (double)cmp, red, NTEAMS, tm, par) + N0;
-        const float T_hi = (float)T;
-        const float T_lo = (float)(T - (double)T_hi);
+        // row total as an FP32 pair: warp sum of the (sum, compensation) pairs, then the team
+        float2 T = warp_sum_df(make_float2(s, cmp));
+        if constexpr (TW > 1) {
+            float2* r = red + (par * NTEAMS + tm.team) * TW;
+            if (tm.lane == 0) r[tm.wit] = T;
+            bar_named(1 + tm.team, TT);
+            T = r[0];
+            for (int w = 1; w < TW; ++w) T = df_add2(T, r[w]);
+            par ^= 1;
+        }
+        T = df_add2(T, N0);
+        const float T_hi = T.x;
+        const float T_lo = T.y;
         float* rrow = R + i * ld_r;
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
@@ -100,7 +110,9 @@ ot_status launch_rates(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const fl
     const float w_log2e = (float)(W / 0.69314718055994530942);
     const int nteams = NTC / (32 * (J <= 1024 ? 1 : (J <= 2048 ? 2 : (J <= 4096 ? 4 : 8))));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((I + nteams - 1) / nteams, 8LL * ctx->num_sms));
-    OTA_ROW_DISPATCH(J, k_rates, <<<grid, NTC, 0, s>>>(G, ld_g, P, I, J, N0, w_log2e, R, ld_r, vec_out));
+    const float n0_hi = (float)N0;
+    const float2 n0 = make_float2(n0_hi, (float)(N0 - (double)n0_hi));
+    OTA_ROW_DISPATCH(J, k_rates, <<<grid, NTC, 0, s>>>(G, ld_g, P, I, J, n0, w_log2e, R, ld_r, vec_out));
     ctx->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "rates launch");
@@ -113,38 +125,43 @@ ot_status launch_rates(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const fl
 __global__ void k_cost(const float* __restrict__ R, int64_t ld_r, int64_t I, int J, float inv_mu,
                        float* __restrict__ C, int64_t ld_c, int pad_inf, int vec_in, int vec_out,
                        unsigned long long* bad) {
-    const int64_t row_ch = (ld_c + 3) / 4;  // chunks per output row (incl. padding)
-    const int64_t n = I * row_ch;
+    const int row_ch = (int)((ld_c + 3) / 4);  // chunks per output row (incl. padding)
+    const int rpb = max(1, (int)blockDim.x / row_ch);  // rows handled together by one block
+    const int sub = threadIdx.x / row_ch;
+    const int ch0 = threadIdx.x - sub * row_ch;
     unsigned long long nbad = 0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / row_ch;
-        const int col = (int)(t - i * row_ch) * 4;
-        float r[4];
-        if (vec_in && col + 4 <= J) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(R + i * ld_r + col));
-            r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
-        } else {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) r[c] = (col + c < J) ? __ldg(R + i * ld_r + col + c) : 1.0f;
-        }
-        float o[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (col + c < J) {
-                const bool ok = r[c] > 0.0f && isfinite(r[c]);
-                nbad += !ok;
-                o[c] = __fdiv_rn(inv_mu, r[c]);
+    for (int64_t i0 = (int64_t)blockIdx.x * rpb; i0 < I; i0 += (int64_t)gridDim.x * rpb) {
+        const int64_t i = i0 + sub;
+        if (sub >= rpb || i >= I) continue;
+        for (int ch = (rpb > 1 ? ch0 : (int)threadIdx.x); ch < row_ch; ch += (rpb > 1 ? row_ch : (int)blockDim.x)) {
+            const int col = ch * 4;
+            float r[4];
+            if (vec_in && col + 4 <= J) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(R + i * ld_r + col));
+                r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
             } else {
-                o[c] = INFINITY;
-            }
-        }
-        float* crow = C + i * ld_c;
-        if (vec_out && col + 4 <= ld_c && (pad_inf || col + 4 <= J)) {
-            *reinterpret_cast<float4*>(crow + col) = make_float4(o[0], o[1], o[2], o[3]);
-        } else {
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (col + c < J || (pad_inf && col + c < ld_c)) crow[col + c] = o[c];
+                for (int c = 0; c < 4; ++c) r[c] = (col + c < J) ? __ldg(R + i * ld_r + col + c) : 1.0f;
+            }
+            float o[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (col + c < J) {
+                    const bool ok = r[c] > 0.0f && isfinite(r[c]);
+                    nbad += !ok;
+                    o[c] = __fdiv_rn(inv_mu, r[c]);
+                } else {
+                    o[c] = INFINITY;
+                }
+            }
+            float* crow = C + i * ld_c;
+            if (vec_out && col + 4 <= ld_c && (pad_inf || col + 4 <= J)) {
+                *reinterpret_cast<float4*>(crow + col) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (col + c < J || (pad_inf && col + c < ld_c)) crow[col + c] = o[c];
+            }
         }
     }
     if (nbad) atomicAdd(bad, nbad);
@@ -155,8 +172,9 @@ ot_status launch_cost(ot_assoc_ctx* ctx, const float* R, int64_t ld_r, int64_t I
     const int vec_in = (ld_r % 4 == 0) && !((uintptr_t)R & 15u);
     const int vec_out = (ld_c % 4 == 0) && !((uintptr_t)C & 15u);
     const float inv_mu = (float)(1.0 / mu);
-    const int64_t n = I * ((ld_c + 3) / 4);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16LL * ctx->num_sms));
+    const int64_t row_ch = (ld_c + 3) / 4;
+    const int64_t rpb = std::max<int64_t>(1, 256 / row_ch);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((I + rpb - 1) / rpb, 16LL * ctx->num_sms));
     k_cost<<<grid, 256, 0, s>>>(R, ld_r, I, J, inv_mu, C, ld_c, pad_inf ? 1 : 0, vec_in, vec_out, bad_dev);
     ctx->launches += 1;
     cudaError_t e = cudaGetLastError();
@@ -217,7 +235,6 @@ __global__ void __launch_bounds__(NTC) k_lambda_part(const int32_t* __restrict__
                                                      double* __restrict__ tpart) {
     __shared__ int32_t sa[MS_ROWS];
     __shared__ float sl[MS_ROWS];
-    __shared__ double sred[NTC / 32];
     const int64_t r0 = (int64_t)blockIdx.x * MS_ROWS;
     const int nrow = (int)std::min<int64_t>(MS_ROWS, I - r0);
     double tl = 0.0;
@@ -237,7 +254,6 @@ __global__ void __launch_bounds__(NTC) k_lambda_part(const int32_t* __restrict__
             if (sa[k] == j) a += (double)sl[k];
         part[(int64_t)blockIdx.x * J + j] = a;
     }
-    (void)sred;
 }
 
 __global__ void k_lambda_sum(const double* __restrict__ part, const double* __restrict__ tpart, int nblk,

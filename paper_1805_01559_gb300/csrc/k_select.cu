@@ -50,29 +50,47 @@ __global__ void __launch_bounds__(256) rs_hist(const float* __restrict__ x, int6
     const uint32_t p0 = st->prefix[0], p1 = st->prefix[1];
     const int two = st->two;
     const int hs = RS_BITS * pass;  // bits already fixed
-    auto add = [&](float f) {
+    // Warp-aggregated histogram update: lanes holding the same digit add once through a
+    // leader, so heavily populated bins do not serialise 32 atomics.
+    const int lane = threadIdx.x & 31;
+    auto add = [&](float f, bool valid) {
         const uint32_t k = fkey(f);
         const uint32_t hi = hs ? (k >> (32 - hs)) : 0u;
         const uint32_t d = (k >> shift) & (RS_BINS - 1);
-        if (hi == p0) atomicAdd(&h[0][d], 1u);
-        if (two && hi == p1) atomicAdd(&h[1][d], 1u);
+        for (int t = 0; t < 1 + two; ++t) {
+            const bool in = valid && hi == (t ? p1 : p0);
+            const uint32_t key = in ? d : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, key);
+            if (in && lane == __ffs(peers) - 1) atomicAdd(&h[t][d], (unsigned)__popc(peers));
+        }
     };
     const int64_t cch = (cols + 3) / 4;
     const int64_t n = rows * cch;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = t / cch;
-        const int64_t c = (t - r * cch) * 4;
+    // whole warps walk the index space together (the aggregation needs converged warps)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); t0 < n; t0 += stride) {
+        const int64_t t = t0 + lane;
+        const bool live = t < n;
+        const int64_t r = live ? t / cch : 0;
+        const int64_t c = live ? (t - r * cch) * 4 : 0;
         const float* row = x + r * ld;
-        if (vec && c + 4 <= cols) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(row + c));
-            add(v.x);
-            add(v.y);
-            add(v.z);
-            add(v.w);
-        } else {
-            for (int e = 0; e < 4; ++e)
-                if (c + e < cols) add(__ldg(row + c + e));
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool ok[4] = {false, false, false, false};
+        if (live) {
+            if (vec && c + 4 <= cols) {
+                v = __ldg(reinterpret_cast<const float4*>(row + c));
+                ok[0] = ok[1] = ok[2] = ok[3] = true;
+            } else {
+                if (c + 0 < cols) { v.x = __ldg(row + c + 0); ok[0] = true; }
+                if (c + 1 < cols) { v.y = __ldg(row + c + 1); ok[1] = true; }
+                if (c + 2 < cols) { v.z = __ldg(row + c + 2); ok[2] = true; }
+                if (c + 3 < cols) { v.w = __ldg(row + c + 3); ok[3] = true; }
+            }
         }
+        add(v.x, ok[0]);
+        add(v.y, ok[1]);
+        add(v.z, ok[2]);
+        add(v.w, ok[3]);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < RS_BINS; t += blockDim.x) {

@@ -5,21 +5,26 @@
 //   G_j    = g_j * k                    column potential (b_j = 2^G_j)
 //   F'_i   = f_i * k - log2 p_i         row potential relative to the row mass
 //   t_ij   = 2^(F'_i + G_j - k C_ij)    = pi_ij / p_i of the current plan
-// Iteration 1 is the exact log-domain step from b = 1 (or a warm-start b): a row
-// log-sum-exp with the row maximum factored out, then a column log-sum-exp with an
-// online (max, sum) pair per column, so no column can underflow however far the
-// starting potentials are.  From then on every plan pi^(k-1) has exact columns
-// (sum q_j <= 1) and rows >= p_i * min q, so iteration k can work directly on
-// t_ij = pi^(k-1)_ij / p_i: one read of C and ONE exp per cell give
-//   a-update:  r_i = sum_j t_ij,  F'_i <- F'_i - log2 r_i       (Alg. 1, a-line)
-//   b-update:  s_j = sum_i t_ij p^_i / r_i,  G_j <- G_j + log2 q^_j - log2 s_j
-//                                                                (Alg. 1, b-line)
-// and r_i also yields the row residual of pi^(k-1) for the stopping test, one sweep
-// late: when it passes, the previous iterate (kept in the other F buffer) is
-// returned, which is the iterate Algorithm 1's loop test examines.
-// Row potentials are kept in FP64 and enter each cell as an FP32 hi/lo pair whose large
-// part cancels against C k_hi inside an exact FMA product; column potentials enter as the
-// FP32 value G_used and are updated in FP64 from that value, so rounding never accumulates.
+//
+// One persistent cooperative launch does the whole iteration:
+//   setup      marginal sums and checks, starting column potentials (b = 1 or warm start);
+//   sweep 1    the exact log-domain first iteration: a row log-sum-exp with the row maximum
+//              factored out, then a column log-sum-exp kept as an online (max, sum) pair per
+//              column, so no column can underflow however far the start is;
+//   sweeps 2.. every plan pi^(k-1) now has exact columns (sum q_j <= 1) and rows
+//              >= p_i min q, so iteration k works on t_ij = pi^(k-1)_ij / p_i directly: one
+//              read of C and ONE exp per cell give
+//                a-update  r_i = sum_j t_ij,                 F'_i <- F'_i - log2 r_i
+//                b-update  s_j = sum_i t_ij p^_i / r_i,      G_j <- G_j + log2 q^_j - log2 s_j
+//              and r_i is also the row sum of pi^(k-1): the loop test ("while accuracy") on
+//              that plan's row residual is one sweep late, so the previous F' (the other
+//              shared-memory buffer) is what a stop returns.
+// Each CTA owns a fixed block-aligned range of rows for the whole solve; its row potentials
+// (an FP32 hi/lo pair, updated with error-free FP32 two-sums) and p^ live in shared memory.
+// A producer warp streams the CTA's rows of C through a ring of shared-memory stages with
+// bulk copies (TMA); it runs on into the next sweep while the consumers are in a grid
+// barrier (C never changes).  Column partials are combined per CTA in team order and
+// across CTAs in CTA order, so reruns are bit-identical.  Every wait is bounded.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -32,15 +37,14 @@
 
 namespace ota {
 
-static constexpr int NT = 256;    // threads per CTA, sweep kernels
-static constexpr int NT_F = 512;  // threads per CTA, finalize kernel (one team per row)
+static constexpr int NT_F = 256;  // threads per CTA of the finalize kernel (row blocks)
 static constexpr double LN2 = 0.69314718055994530942;
 static constexpr double LOG2E = 1.44269504088896340736;
 
 enum : int { DEV_ENUMERIC = -7 };
 
 struct DevScalars {
-    double sp, sq;          // sums of the caller's p and q
+    double sp, sq;  // sums of the caller's p and q
     double inv_sp, inv_sq;
     float inv_sp_f;
     int status;
@@ -64,18 +68,30 @@ __device__ __forceinline__ void load_G(const double* __restrict__ G, int J, int 
     }
 }
 
-// Cell exponent x = F + G - k C in log2 units, with F = F_hi + F_lo (a float pair holding
-// the FP64 row potential) and k = k_hi + k_lo.  The exact FMA product cancels the large
-// parts F_hi - C k_hi first, so the only roundings happen at the magnitude of |G| and |x|,
-// however large k C and F are on the support.  k_lo > 0 always (see split_k), so a +inf
-// cost (masked column, forbidden link) gives -inf and never inf - inf.
+// Cell exponent x = F + G - k C in log2 units, with F = F_hi + F_lo (FP32 pair) and
+// k = k_hi + k_lo.  The exact FMA product cancels the large parts F_hi - C k_hi first, so
+// the only roundings happen at the magnitude of |G| and |x|, however large k C and F are on
+// the support.  k_lo > 0 always (see split_k): a +inf cost (masked column, forbidden link)
+// gives -inf and never inf - inf.
 __device__ __forceinline__ float expo(float F_hi, float F_lo_plus_G, float c, float k_hi, float k_lo) {
     return fmaf(-c, k_hi, F_hi) + fmaf(-c, k_lo, F_lo_plus_G);
 }
 
-__device__ __forceinline__ void split_f(double F, float* hi, float* lo) {
-    *hi = (float)F;
-    *lo = (float)(F - (double)*hi);
+// Error-free sum a + b = s + e (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) - d as a renormalised FP32 pair.
+__device__ __forceinline__ float2 df_sub(float2 f, float d) {
+    float s, e;
+    two_sum(f.x, -d, s, e);
+    e += f.y;
+    float h, l;
+    two_sum(s, e, h, l);
+    return make_float2(h, l);
 }
 
 // k = k_hi + k_lo with k_hi rounded down and 0 < k_lo <= ulp(k_hi): the low part is never
@@ -90,172 +106,123 @@ static void split_k(double k, float* hi, float* lo) {
 }
 
 // ------------------------------------------------------------------------------------------
-// prep: sums and validity of the marginals, starting column potentials.
+// Row streaming: one producer warp copies contiguous blocks of rows of C into a ring of
+// shared-memory stages with bulk copies; the consumer warps work on them.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) sk_prep(const float* __restrict__ p, const float* __restrict__ q,
-                                                int64_t I, int J, const double* __restrict__ g_warm,
-                                                double k, const unsigned long long* __restrict__ input_bad,
-                                                DevScalars* sc, double* G) {
-    __shared__ double sh_p[32], sh_q[32];
-    __shared__ int sh_bad;
-    if (threadIdx.x == 0) sh_bad = 0;
-    __syncthreads();
-    double sp = 0.0, sq = 0.0;
-    int bad = 0;
-    for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
-        const float v = p[i];
-        bad |= !(v > 0.0f) || !isfinite(v);
-        sp += (double)v;
-    }
-    for (int j = threadIdx.x; j < J; j += blockDim.x) {
-        const float v = q[j];
-        bad |= !(v > 0.0f) || !isfinite(v);
-        sq += (double)v;
-        G[j] = g_warm ? g_warm[j] * k : 0.0;
-        if (g_warm && !isfinite(g_warm[j])) bad = 1;
-    }
-    sp = warp_sum(sp);
-    sq = warp_sum(sq);
-    if ((threadIdx.x & 31) == 0) {
-        sh_p[threadIdx.x >> 5] = sp;
-        sh_q[threadIdx.x >> 5] = sq;
-    }
-    if (bad) atomicOr(&sh_bad, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tp = 0.0, tq = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            tp += sh_p[w];
-            tq += sh_q[w];
-        }
-        int st = DEV_OK;
-        if (sh_bad || !(fabs(tp - tq) <= 1e-5 * tp) || (input_bad && *input_bad)) st = DEV_EINVAL;
-        sc->sp = tp;
-        sc->sq = tq;
-        sc->inv_sp = 1.0 / tp;
-        sc->inv_sq = 1.0 / tq;
-        sc->inv_sp_f = (float)(1.0 / tp);
-        sc->status = st;
-    }
+// Consumer warps per CTA: 12 (3 per SM sub-partition, so 13 warps keep 128 registers each)
+// when a team is 1, 2 or 4 warps; 8 when a row needs a team of 8 warps.
+template <int TW>
+struct Cons {
+    static constexpr int NCW = (TW == 8) ? 8 : 12;
+    static constexpr int NT = 32 * (NCW + 1);  // + one producer warp
+};
+static constexpr int MAX_STAGES = 8;
+static constexpr int CONS_BAR = 15;          // named barrier of the consumer warps
+static constexpr int SMEM_HDR = 256;         // mbarriers at the start of dynamic smem
+
+struct StreamCfg {
+    int rows_per_stage;  // NTEAMS * rpt
+    int rpt;             // rows per team per stage
+    int stages;
+    int stage_floats;    // rows_per_stage * ld
+    int rmax;            // most rows any CTA owns
+    int off_G;           // byte offsets inside dynamic smem
+    int off_F;
+    int off_P;
+    int off_ring;
+};
+
+// Column potentials as FP32 in shared memory (padding columns 0).
+__device__ __forceinline__ void load_G_smem(const double* __restrict__ G, int J, int Jp, float* Gs, int tid,
+                                            int nthreads) {
+    for (int j = tid; j < Jp; j += nthreads) Gs[j] = (j < J) ? (float)G[j] : 0.0f;
 }
 
-// ------------------------------------------------------------------------------------------
-// Iteration 1, rows: exact row LSE, then per-column online (max, sum) of log2 pi^(1/2).
-// ------------------------------------------------------------------------------------------
+// log2(r) for the row and column corrections: a short series when r is within 2^-7 of 1
+// (|u|^5/5 < 2^-37 relative to the result), the SFU logarithm otherwise.
+__device__ __forceinline__ float log2_corr(float r) {
+    const float u = r - 1.0f;  // exact for r in [0.5, 2]
+    const float series = u * (1.0f + u * (-0.5f + u * (0.33333334f + u * -0.25f))) * 1.44269504f;
+    const float sfu = __log2f(r);
+    return fabsf(u) < 0.0078125f ? series : sfu;
+}
+
+// A lane's chunk v is certainly inside the row when the dispatch chose VPT = ceil(J4 / 32)
+// for a one-warp team (pick_kernels does exactly that for TW = 1): then every chunk but the
+// lane's last ends at or before column J.  Wider teams check every chunk.
 template <int TW, int VPT>
-__global__ void __launch_bounds__(NT) sk_init_rows(const float* __restrict__ C, int64_t ld, int64_t I,
-                                                   int J, int Jp, const float* __restrict__ p,
-                                                   const DevScalars* __restrict__ sc,
-                                                   const double* __restrict__ G0, double* __restrict__ F1,
-                                                   float2* __restrict__ part, float k_hi, float k_lo) {
-    constexpr int TT = 32 * TW, NTEAMS = NT / TT;
-    extern __shared__ float4 dyn_smem[];
-    float2* comb = reinterpret_cast<float2*>(dyn_smem);  // [NTEAMS][Jp]
-    __shared__ float red[2 * NTEAMS * TW];
-    const Team<TW> tm;
-    if (sc->status != DEV_OK) return;
-    const int nb = gridDim.x, b = blockIdx.x;
-    const int64_t r0 = I * b / nb, r1 = I * (b + 1) / nb;
-    float4 g[VPT], M[VPT], S[VPT];
-    load_G<TW, VPT>(G0, J, tm.tl, g);
+__device__ __forceinline__ constexpr bool chunk_inside(int v) {
+    return TW == 1 && v < VPT - 1;
+}
+
+// Row load from a shared-memory stage; chunks that can leave the row are checked.
+template <int TW, int VPT>
+__device__ __forceinline__ void load_row_smem(const float* row, int J, int tl, float4 (&x)[VPT]) {
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-        M[v] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
-        S[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const float inv_sp = sc->inv_sp_f;
-    int par = 0;
-    for (int64_t i = r0 + tm.team; i < r1; i += NTEAMS) {
-        float4 x[VPT];
-        load_row<TW, VPT>(C + i * ld, J, tm.tl, x);
-        // row maximum of y = G0 - k C (approximate values suffice for the shift)
-        float m = -INFINITY;
-#pragma unroll
-        for (int v = 0; v < VPT; ++v)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) m = fmaxf(m, fmaf(-comp(x[v], c), k_hi, comp(g[v], c)));
-        m = team_reduce<TW, float, true>(m, red, NTEAMS, tm, par);
-        // z = y - m formed with the large parts cancelled by the exact product
-        float s = 0.f;
-#pragma unroll
-        for (int v = 0; v < VPT; ++v)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float z = expo(-m, comp(g[v], c), comp(x[v], c), k_hi, k_lo);
-                comp(x[v], c) = z;
-                s += ex2(z);
+        const int col = 4 * (tl + 32 * TW * v);
+        if (chunk_inside<TW, VPT>(v)) {
+            x[v] = *reinterpret_cast<const float4*>(row + col);
+        } else if (col < J) {
+            float4 t = *reinterpret_cast<const float4*>(row + col);
+            if (col + 4 > J) {
+                if (col + 1 >= J) t.y = INFINITY;
+                if (col + 2 >= J) t.z = INFINITY;
+                if (col + 3 >= J) t.w = INFINITY;
             }
-        s = team_reduce<TW, float, false>(s, red, NTEAMS, tm, par);
-        const float ls = log2f(s);
-        if (tm.tl == 0) F1[i] = -((double)m + (double)ls);   // F'^1 = -LSE2_j(y)
-        const float cst = log2f(__ldg(p + i) * inv_sp) - ls;
-#pragma unroll
-        for (int v = 0; v < VPT; ++v)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float u = comp(x[v], c) + cst;  // log2 pi^(1/2)_ij = z - log2 s + log2 p^
-                float& Mc = comp(M[v], c);
-                float& Sc = comp(S[v], c);
-                if (u > Mc) {
-                    Sc = fmaf(Sc, ex2(Mc - u), 1.0f);
-                    Mc = u;
-                } else if (u > -INFINITY) {
-                    Sc += ex2(u - Mc);
+            x[v] = t;
+        } else {
+            x[v] = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+        }
+    }
+}
+
+// Producer: stream the CTA's row blocks sweep after sweep until the consumers raise s_stop,
+// then wait for every copy still in flight before leaving.
+__device__ __forceinline__ void stream_rows_producer(const float* C, int64_t ld, int64_t r0, int64_t r1,
+                                                     const StreamCfg& S, float* ring, uint64_t* full,
+                                                     uint64_t* empty, volatile int* s_stop, int* status,
+                                                     long long spin) {
+    const int nblk = (int)((r1 - r0 + S.rows_per_stage - 1) / S.rows_per_stage);
+    uint32_t seq = 0;
+    bool stop = (nblk <= 0);
+    while (!stop) {
+        for (int k = 0; k < nblk && !stop; ++k) {
+            const int st = (int)(seq % (uint32_t)S.stages);
+            const uint32_t use = seq / (uint32_t)S.stages;
+            if (use > 0) {  // wait for the consumers to release this stage's previous copy
+                long long n = 0;
+                while (!mbar_try_wait_sleep(&empty[st], (use - 1) & 1u, 500)) {
+                    if (*s_stop) { stop = true; break; }
+                    if ((++n & 1023) == 0 && ld_volatile_i32(status) != DEV_OK) { stop = true; break; }
+                    if (n > spin) {
+                        atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
+                        stop = true;
+                        break;
+                    }
                 }
+                if (stop) break;
             }
-    }
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-        const int col = 4 * (tm.tl + TT * v);
-        if (col < Jp)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) comb[tm.team * Jp + col + c] = make_float2(comp(M[v], c), comp(S[v], c));
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < J; j += NT) {
-        float m = comb[j].x, s = comb[j].y;
-        for (int t = 1; t < NTEAMS; ++t) {
-            const float2 o = comb[t * Jp + j];
-            lse2_merge(m, s, o.x, o.y);
+            if (*s_stop) { stop = true; break; }
+            const int64_t row0 = r0 + (int64_t)k * S.rows_per_stage;
+            const int rows = (int)min((int64_t)S.rows_per_stage, r1 - row0);
+            const uint32_t bytes = (uint32_t)(rows * ld * (int64_t)sizeof(float));
+            mbar_arrive_expect_tx(&full[st], bytes);
+            bulk_g2s(ring + (size_t)st * S.stage_floats, C + row0 * ld, bytes, &full[st]);
+            ++seq;
         }
-        part[(int64_t)b * Jp + j] = make_float2(m, s);
     }
-}
-
-// Iteration 1, columns: G^1_j = G^0_j + log2 q^_j - log2(column sum of pi^(1/2)).
-__global__ void sk_init_cols(const float2* __restrict__ part, int nb, int Jp, int J,
-                             const float* __restrict__ q, DevScalars* sc, double* G) {
-    if (sc->status != DEV_OK) return;
-    const int lane = threadIdx.x & 31;
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int j = w; j < J; j += nw) {
-        float m = -INFINITY;
-        for (int bb = lane; bb < nb; bb += 32) m = fmaxf(m, part[(int64_t)bb * Jp + j].x);
-        m = warp_max(m);
-        double s = 0.0;
-        if (m > -INFINITY)
-            for (int bb = lane; bb < nb; bb += 32) {
-                const float2 v = part[(int64_t)bb * Jp + j];
-                if (v.x > -INFINITY) s += (double)v.y * (double)ex2(v.x - m);
-            }
-        s = warp_sum(s);
-        if (lane == 0) {
-            if (!(s > 0.0) || !isfinite(s)) {
-                atomicCAS(&sc->status, DEV_OK, DEV_ENUMERIC);
-            } else {
-                const double Gu = (double)(float)G[j];
-                const double qh = (double)q[j] * sc->inv_sq;
-                G[j] = Gu + log2(qh) - ((double)m + log2(s));
-            }
+    // Leave no copy in flight: wait for the last use of every stage to land.
+    for (int st = 0; st < S.stages; ++st) {
+        if (seq <= (uint32_t)st) continue;
+        const uint32_t uses = (seq - (uint32_t)st + S.stages - 1) / (uint32_t)S.stages;
+        long long n = 0;
+        while (!mbar_try_wait_sleep(&full[st], (uses - 1) & 1u, 1000) && ++n <= spin) {
         }
     }
 }
 
-// ------------------------------------------------------------------------------------------
-// Iterations 2.. : persistent cooperative kernel, one read of C and one ex2 per cell.
-// ------------------------------------------------------------------------------------------
-struct LoopParams {
+struct SolveParams {
     const float* C;
     int64_t ld;
     int64_t I;
@@ -263,137 +230,486 @@ struct LoopParams {
     int Jp;
     const float* p;
     const float* q;
-    const DevScalars* sc;
-    double* F0;
-    double* F1;
-    double* G;
-    float* colpart;   // [nb][Jp]
-    double* errpart;  // [nb]
+    const double* g_warm;                 // warm-start g (natural units) or nullptr
+    const unsigned long long* input_bad;  // nonzero => invalid rates upstream, or nullptr
+    DevScalars* sc;
     LoopState* st;
+    double* G;        // [3][Jp]: column potentials G^k (log2 units, FP64) in buffer k & 1,
+                      // then log2 q^_j (set once per solve)
+    float2* F_out;    // [I] row potentials of the returned plan (hi, lo)
+    float* colpart;   // [nb][2 * Jp]
+    double* errpart;  // [nb] during setup (sums of p); reused as float2 [nb] residual pairs
+    double k;
     float k_hi, k_lo;
     double tol;
     int max_iter;
     long long spin;
 };
 
+// Block-aligned row range of CTA b.
+__device__ __forceinline__ void cta_rows(int64_t I, int rs, int b, int nb, int64_t* r0, int64_t* r1) {
+    const int64_t B = (I + rs - 1) / rs;
+    *r0 = (B * b / nb) * rs;
+    *r1 = min(I, (B * (b + 1) / nb) * (int64_t)rs);
+}
+
 template <int TW, int VPT>
-__global__ void __launch_bounds__(NT, 2) sk_loop(LoopParams P) {
-    constexpr int TT = 32 * TW, NTEAMS = NT / TT;
-    extern __shared__ float4 dyn_smem[];
-    float* comb = reinterpret_cast<float*>(dyn_smem);  // [NTEAMS][Jp]
+__global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve(SolveParams P, StreamCfg S) {
+    constexpr int NCW = Cons<TW>::NCW;
+    constexpr int TT = 32 * TW, NTEAMS = NCW / TW, NC = NCW * 32;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
+    uint64_t* empty = full + MAX_STAGES;
+    float* comb = reinterpret_cast<float*>(dyn + SMEM_HDR);    // [ceil(NTEAMS / 2)][Jp]
+    float* Gs = reinterpret_cast<float*>(dyn + S.off_G);       // [Jp]
+    float2* Fs = reinterpret_cast<float2*>(dyn + S.off_F);     // [2][rmax]
+    float* Ps = reinterpret_cast<float*>(dyn + S.off_P);       // [rmax]
+    float* ring = reinterpret_cast<float*>(dyn + S.off_ring);  // [stages][stage_floats]
     __shared__ float red[2 * NTEAMS * TW];
-    __shared__ double errs[NTEAMS];
-    __shared__ int s_stop;
-    const Team<TW> tm;
-    if (P.sc->status != DEV_OK) return;
-    const int J = P.J, Jp = P.Jp;
+    __shared__ float errf[NTEAMS];
+    __shared__ double sh_sum[NCW][2];
+    __shared__ int s_dec, s_ok, s_bad;
+    __shared__ volatile int s_stop;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = gridDim.x, b = blockIdx.x;
-    const int warp = threadIdx.x >> 5;
-    const int64_t r0 = P.I * b / nb, r1 = P.I * (b + 1) / nb;
-    const float inv_sp = P.sc->inv_sp_f;
-    float4 g[VPT];
-    load_G<TW, VPT>(P.G, J, tm.tl, g);
-    unsigned gen = 0;
-    for (int s = 2;; ++s) {
-        const double* __restrict__ Fold = (s & 1) ? P.F0 : P.F1;  // F^(s-1) lives in buffer (s-1)&1
-        double* __restrict__ Fnew = (s & 1) ? P.F1 : P.F0;
-        float4 acc[VPT];
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-        double errt = 0.0;
-        int par = 0;
-        for (int64_t i = r0 + tm.team; i < r1; i += NTEAMS) {
-            float4 x[VPT];
-            load_row<TW, VPT>(P.C + i * P.ld, J, tm.tl, x);
-            const double Fd = Fold[i];
-            float Fh, Fl;
-            split_f(Fd, &Fh, &Fl);
-            float rs = 0.f;
-#pragma unroll
-            for (int v = 0; v < VPT; ++v)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float t = ex2(expo(Fh, Fl + comp(g[v], c), comp(x[v], c), P.k_hi, P.k_lo));
-                    comp(x[v], c) = t;
-                    rs += t;
-                }
-            rs = team_reduce<TW, float, false>(rs, red, NTEAMS, tm, par);
-            const float ph = __ldg(P.p + i) * inv_sp;
-            if (tm.tl == 0) {
-                Fnew[i] = Fd - (double)log2_rel(rs);
-                errt += (double)ph * fabs((double)rs - 1.0);
-            }
-            const float d = ph / rs;
-#pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                acc[v].x = fmaf(x[v].x, d, acc[v].x);
-                acc[v].y = fmaf(x[v].y, d, acc[v].y);
-                acc[v].z = fmaf(x[v].z, d, acc[v].z);
-                acc[v].w = fmaf(x[v].w, d, acc[v].w);
-            }
+    int64_t r0, r1;
+    cta_rows(P.I, S.rows_per_stage, b, nb, &r0, &r1);
+    const int nrow = (int)max((int64_t)0, r1 - r0);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
         }
-        // CTA combine of the column partials, teams in a fixed order.
+        s_stop = 0;
+        s_bad = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == NCW) {
+        if (lane == 0)
+            stream_rows_producer(P.C, P.ld, r0, r1, S, ring, full, empty, &s_stop, &P.st->status, P.spin);
+        return;
+    }
+    int* status = &P.st->status;
+    const int J = P.J, Jp = P.Jp;
+    const int tid = threadIdx.x;
+    unsigned gen = 0;
+#define OTA_BARRIER()                                                                                    \
+    do {                                                                                                \
+        if (!grid_barrier_named(&P.st->bar, (unsigned)nb * ++gen, status, P.spin, CONS_BAR, NC, &s_ok)) { \
+            if (tid == 0) s_stop = 1;                                                                   \
+            return;                                                                                     \
+        }                                                                                               \
+    } while (0)
+
+    // ---- setup: sums of p (per CTA) and q (every CTA), checks, starting G ----------------
+    {
+        double sp = 0.0;
+        int bad = 0;
+        for (int r = tid; r < nrow; r += NC) {
+            const float v = __ldg(P.p + r0 + r);
+            bad |= !(v > 0.0f) || !isfinite(v);
+            sp += (double)v;
+            Ps[r] = v;
+        }
+        const int gw = b * NCW + warp, nw = nb * NCW;
+        for (int j = gw * 32 + lane; j < J; j += nw * 32) {
+            const double g0 = P.g_warm ? P.g_warm[j] * P.k : 0.0;
+            bad |= !isfinite(g0);
+            P.G[j] = g0;
+        }
+        if (b == 0 && tid == 0 && P.input_bad && *P.input_bad) bad = 1;
+        sp = warp_sum(sp);
+        if (lane == 0) sh_sum[warp][0] = sp;
+        if (bad) atomicOr(&s_bad, 1);
+        bar_named(CONS_BAR, NC);
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NCW; ++w) t += sh_sum[w][0];
+            P.errpart[b] = t;
+            if (s_bad) atomicCAS(status, DEV_OK, DEV_EINVAL);
+        }
+    }
+    OTA_BARRIER();
+    double sp = 0.0, sq = 0.0;
+    {
+        // every CTA forms the same totals in the same order
+        double a = 0.0, c = 0.0;
+        int badq = 0;
+        for (int bb = tid; bb < nb; bb += NC) a += P.errpart[bb];
+        for (int j = tid; j < J; j += NC) {
+            const float v = __ldg(P.q + j);
+            badq |= !(v > 0.0f) || !isfinite(v);
+            c += (double)v;
+        }
+        a = warp_sum(a);
+        c = warp_sum(c);
+        if (tid == 0) s_bad = 0;
+        bar_named(CONS_BAR, NC);
+        if (lane == 0) {
+            sh_sum[warp][0] = a;
+            sh_sum[warp][1] = c;
+        }
+        if (badq) atomicOr(&s_bad, 1);
+        bar_named(CONS_BAR, NC);
+        for (int w = 0; w < NCW; ++w) {
+            sp += sh_sum[w][0];
+            sq += sh_sum[w][1];
+        }
+        if (s_bad || !(fabs(sp - sq) <= 1e-5 * sp)) {
+            if (b == 0 && tid == 0) atomicCAS(status, DEV_OK, DEV_EINVAL);
+            if (tid == 0) s_stop = 1;
+            return;  // the same decision in every CTA
+        }
+        if (b == 0 && tid == 0) {
+            P.sc->sp = sp;
+            P.sc->sq = sq;
+            P.sc->inv_sp = 1.0 / sp;
+            P.sc->inv_sq = 1.0 / sq;
+            P.sc->inv_sp_f = (float)(1.0 / sp);
+            P.sc->status = DEV_OK;
+        }
+    }
+    const double inv_sq = 1.0 / sq;
+    double* LQ = P.G + 2 * Jp;  // log2 q^_j, formed once here (read after the next grid barrier)
+    {
+        const int gw = b * NCW + warp, nw = nb * NCW;
+        for (int j = gw * 32 + lane; j < J; j += nw * 32) LQ[j] = log2((double)__ldg(P.q + j) * inv_sq);
+        const float inv_sp_f = (float)(1.0 / sp);
+        for (int r = tid; r < nrow; r += NC) Ps[r] *= inv_sp_f;  // p^_i
+        bar_named(CONS_BAR, NC);
+    }
+    const Team<TW> tm;
+    const int nblk = (nrow + S.rows_per_stage - 1) / S.rows_per_stage;
+    load_G_smem(P.G, J, Jp, Gs, tid, NC);
+    bar_named(CONS_BAR, NC);
+    uint32_t cseq = 0;
+    int par = 0;
+
+    // ---- sweep 1: exact log-domain iteration ------------------------------------------
+    {
+        float4 M[VPT], Sm[VPT];
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
-            const int col = 4 * (tm.tl + TT * v);
-            if (col < Jp) *reinterpret_cast<float4*>(comb + tm.team * Jp + col) = acc[v];
+            M[v] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+            Sm[v] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (tm.tl == 0) errs[tm.team] = errt;
-        __syncthreads();
-        for (int j = threadIdx.x; j < J; j += NT) {
-            float sum = comb[j];
-            for (int t = 1; t < NTEAMS; ++t) sum += comb[t * Jp + j];
-            P.colpart[(int64_t)b * Jp + j] = sum;
+        float2* F1 = Fs + S.rmax;  // F'^1 lives in buffer 1
+        for (int kb = 0; kb < nblk; ++kb) {
+            const int st = (int)(cseq % (uint32_t)S.stages);
+            const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
+            const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, status);
+            const int lr0 = kb * S.rows_per_stage;
+            const int rows = min(S.rows_per_stage, nrow - lr0);
+            const float* stage = ring + (size_t)st * S.stage_floats;
+            for (int j = 0; ok && j < S.rpt; ++j) {
+                const int rr = tm.team + NTEAMS * j;
+                if (rr >= rows) break;
+                float4 x[VPT];
+                load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
+                // row maximum of y = G0 - k C (approximate values suffice for the shift)
+                float m = -INFINITY;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    float4 gv = col < Jp ? *reinterpret_cast<const float4*>(Gs + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) m = fmaxf(m, fmaf(-comp(x[v], c), P.k_hi, comp(gv, c)));
+                }
+                m = team_reduce<TW, float, true>(m, red, NTEAMS, tm, par);
+                // z = y - m with the large parts cancelled by the exact product
+                float s = 0.f;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    float4 gv = col < Jp ? *reinterpret_cast<const float4*>(Gs + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float z = expo(-m, comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo);
+                        comp(x[v], c) = z;
+                        s += ex2(z);
+                    }
+                }
+                s = team_reduce<TW, float, false>(s, red, NTEAMS, tm, par);
+                const float ls = log2f(s);
+                if (tm.tl == 0) {  // F'^1 = -LSE2_j(y) = -(m + log2 s), exact as an FP32 pair
+                    float hi, lo;
+                    two_sum(m, ls, hi, lo);
+                    F1[lr0 + rr] = make_float2(-hi, -lo);
+                }
+                const float cst = log2f(Ps[lr0 + rr]) - ls;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float u = comp(x[v], c) + cst;  // log2 pi^(1/2)_ij
+                        float& Mc = comp(M[v], c);
+                        float& Sc = comp(Sm[v], c);
+                        if (u > Mc) {
+                            Sc = fmaf(Sc, ex2(Mc - u), 1.0f);
+                            Mc = u;
+                        } else if (u > -INFINITY) {
+                            Sc += ex2(u - Mc);
+                        }
+                    }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+            ++cseq;
         }
-        if (threadIdx.x == 0) {
-            double e = errs[0];
-            for (int t = 1; t < NTEAMS; ++t) e += errs[t];
-            P.errpart[b] = e;
-        }
-        if (!grid_barrier(&P.st->bar, (unsigned)nb * ++gen, &P.st->status, P.spin)) return;
-        // Loop test on pi^(s-1): every CTA forms the same total in the same order.
-        if (warp == 0) {
-            double e = 0.0;
-            for (int bb = tm.lane; bb < nb; bb += 32) e += P.errpart[bb];
-            e = warp_sum(e);
-            if (tm.lane == 0) {
-                const int stop = (e <= P.tol) || (s - 1 >= P.max_iter);
-                s_stop = stop;
-                if (stop && b == 0) {
-                    P.st->iters = s - 1;
-                    P.st->err = e;
-                    P.st->converged = (e <= P.tol);
+        // CTA merge of the (max, sum) pairs in two rounds through the float buffer: the column
+        // maxima first (kept in Gs, which is reloaded after the next grid barrier anyway),
+        // then the sums rescaled to them; teams in a fixed order.
+        constexpr int HALF = (NTEAMS + 1) / 2;
+        for (int round = 0; round < 2; ++round) {  // the first half stores, the second half merges
+            if ((tm.team < HALF) == (round == 0)) {
+                const int slot = round == 0 ? tm.team : tm.team - HALF;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    if (col < Jp) {
+                        float4* d = reinterpret_cast<float4*>(comb + slot * Jp + col);
+                        if (round == 0) {
+                            *d = M[v];
+                        } else {
+                            float4 o = *d;
+                            o.x = fmaxf(o.x, M[v].x);
+                            o.y = fmaxf(o.y, M[v].y);
+                            o.z = fmaxf(o.z, M[v].z);
+                            o.w = fmaxf(o.w, M[v].w);
+                            *d = o;
+                        }
+                    }
                 }
             }
+            bar_named(CONS_BAR, NC);
         }
-        __syncthreads();
-        if (s_stop) return;
-        // b-update, one warp per column.
+        for (int j = tid; j < Jp; j += NC) {
+            float mm = comb[j];
+            for (int t = 1; t < HALF; ++t) mm = fmaxf(mm, comb[t * Jp + j]);
+            Gs[j] = mm;
+        }
+        bar_named(CONS_BAR, NC);
+        for (int round = 0; round < 2; ++round) {
+            if ((tm.team < HALF) == (round == 0)) {
+                const int slot = round == 0 ? tm.team : tm.team - HALF;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    if (col < Jp) {
+                        float4 sc;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float Mc = comp(M[v], c), mm = Gs[col + c];
+                            comp(sc, c) = Mc > -INFINITY ? comp(Sm[v], c) * ex2(Mc - mm) : 0.f;
+                        }
+                        float4* d = reinterpret_cast<float4*>(comb + slot * Jp + col);
+                        if (round == 0) {
+                            *d = sc;
+                        } else {
+                            float4 o = *d;
+                            o.x += sc.x;
+                            o.y += sc.y;
+                            o.z += sc.z;
+                            o.w += sc.w;
+                            *d = o;
+                        }
+                    }
+                }
+            }
+            bar_named(CONS_BAR, NC);
+        }
+        float2* part2 = reinterpret_cast<float2*>(P.colpart);
+        for (int j = tid; j < J; j += NC) {
+            float ss = comb[j];
+            for (int t = 1; t < HALF; ++t) ss += comb[t * Jp + j];
+            part2[(int64_t)b * Jp + j] = make_float2(Gs[j], ss);
+        }
+        OTA_BARRIER();
+        // G^1_j = G^0_j + log2 q^_j - log2(column sum of pi^(1/2)), one warp per column
         {
-            const int gw = b * (NT / 32) + warp, nw = nb * (NT / 32);
+            const int gw = b * NCW + warp, nw = nb * NCW;
             for (int j = gw; j < J; j += nw) {
-                double sum = 0.0;
-                for (int bb = tm.lane; bb < nb; bb += 32) sum += (double)P.colpart[(int64_t)bb * Jp + j];
-                sum = warp_sum(sum);
-                if (tm.lane == 0) {
-                    if (!(sum > 0.0) || !isfinite(sum)) {
-                        atomicCAS(&P.st->status, DEV_OK, DEV_ENUMERIC);
+                float mm = -INFINITY;
+                for (int bb = lane; bb < nb; bb += 32) mm = fmaxf(mm, part2[(int64_t)bb * Jp + j].x);
+                mm = warp_max(mm);
+                double ss = 0.0;
+                if (mm > -INFINITY)
+                    for (int bb = lane; bb < nb; bb += 32) {
+                        const float2 o = part2[(int64_t)bb * Jp + j];
+                        if (o.x > -INFINITY) ss += (double)o.y * (double)ex2(o.x - mm);
+                    }
+                ss = warp_sum(ss);
+                if (lane == 0) {
+                    if (!(ss > 0.0) || !isfinite(ss)) {
+                        atomicCAS(status, DEV_OK, DEV_ENUMERIC);
                     } else {
                         const double Gu = (double)(float)P.G[j];
-                        const double qh = (double)__ldg(P.q + j) * P.sc->inv_sq;
-                        P.G[j] = Gu + log2(qh) - log2(sum);
+                        P.G[Jp + j] = Gu + LQ[j] - ((double)mm + log2(ss));
                     }
                 }
             }
         }
-        if (!grid_barrier(&P.st->bar, (unsigned)nb * ++gen, &P.st->status, P.spin)) return;
-        load_G<TW, VPT>(P.G, J, tm.tl, g);
+        OTA_BARRIER();
+        load_G_smem(P.G + Jp, J, Jp, Gs, tid, NC);
+        bar_named(CONS_BAR, NC);
     }
+
+    // ---- sweeps 2, 3, ...: one read of C and one ex2 per cell -----------------------------
+    for (int s = 2;; ++s) {
+        const float2* Fold = Fs + ((s - 1) & 1) * S.rmax;  // F'^(s-1)
+        float2* Fnew = Fs + (s & 1) * S.rmax;
+        float4 acc[VPT];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float errt = 0.f;  // every lane of a team holds the same value
+        for (int kb = 0; kb < nblk; ++kb) {
+            const int st = (int)(cseq % (uint32_t)S.stages);
+            const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
+            const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, status);
+            const int lr0 = kb * S.rows_per_stage;
+            const int rows = min(S.rows_per_stage, nrow - lr0);
+            const float* stage = ring + (size_t)st * S.stage_floats;
+            for (int j = 0; ok && j < S.rpt; ++j) {
+                const int rr = tm.team + NTEAMS * j;
+                if (rr >= rows) break;
+                const int lr = lr0 + rr;
+                float4 x[VPT];
+                load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
+                const float2 F = Fold[lr];
+                float rs = 0.f;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    if (chunk_inside<TW, VPT>(v) || col < J) {  // chunks past the row carry no mass
+                        float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float t = ex2(expo(F.x, F.y + comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
+                            comp(x[v], c) = t;
+                            rs += t;
+                        }
+                    } else {
+                        x[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+                rs = team_reduce<TW, float, false>(rs, red, NTEAMS, tm, par);
+                const float ph = Ps[lr];
+                // every lane forms the update (no divergent branch); one lane stores it
+                const float2 Fn = df_sub(F, log2_corr(rs));
+                if (tm.tl == 0) Fnew[lr] = Fn;
+                errt = fmaf(ph, fabsf(rs - 1.0f), errt);
+                const float d = __fdividef(ph, rs);
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    acc[v].x = fmaf(x[v].x, d, acc[v].x);
+                    acc[v].y = fmaf(x[v].y, d, acc[v].y);
+                    acc[v].z = fmaf(x[v].z, d, acc[v].z);
+                    acc[v].w = fmaf(x[v].w, d, acc[v].w);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+            ++cseq;
+        }
+        // CTA combine of the column partials in a fixed order: the first half of the teams
+        // stores, the second half adds its partial onto slot team - NTEAMS/2, then the slots
+        // are summed in order (the buffer holds NTEAMS/2 rows).
+        constexpr int HALF = (NTEAMS + 1) / 2;
+        if (tm.team < HALF) {
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int col = 4 * (tm.tl + TT * v);
+                if (col < Jp) *reinterpret_cast<float4*>(comb + tm.team * Jp + col) = acc[v];
+            }
+        }
+        if (tm.tl == 0) errf[tm.team] = errt;
+        bar_named(CONS_BAR, NC);
+        if (tm.team >= HALF) {
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int col = 4 * (tm.tl + TT * v);
+                if (col < Jp) {
+                    float4* d = reinterpret_cast<float4*>(comb + (tm.team - HALF) * Jp + col);
+                    float4 o = *d;
+                    o.x += acc[v].x;
+                    o.y += acc[v].y;
+                    o.z += acc[v].z;
+                    o.w += acc[v].w;
+                    *d = o;
+                }
+            }
+        }
+        bar_named(CONS_BAR, NC);
+        for (int j = tid; j < J; j += NC) {
+            float sum = comb[j];
+            for (int t = 1; t < HALF; ++t) sum += comb[t * Jp + j];
+            P.colpart[(int64_t)b * Jp + j] = sum;
+        }
+        float2* errp = reinterpret_cast<float2*>(P.errpart);
+        if (tid == 0) {
+            float2 e = make_float2(errf[0], 0.f);
+            for (int t = 1; t < NTEAMS; ++t) e = df_add(e, errf[t]);
+            errp[b] = e;
+        }
+        OTA_BARRIER();
+        // Loop test on pi^(s-1) (warp 0; every CTA forms the same total in the same order)
+        // while the other warps already form G^s into the other buffer: G^(s-1) stays intact
+        // for a stop.  All sums here are FP32 pairs: no FP64 in the per-sweep path.
+        if (warp == 0) {
+            float2 e = make_float2(0.f, 0.f);
+            for (int bb = lane; bb < nb; bb += 32) e = df_add2(e, errp[bb]);
+            e = warp_sum_df(e);
+            if (lane == 0) {
+                const double ed = (double)e.x + (double)e.y;
+                const int stop = (ed <= P.tol) || (s - 1 >= P.max_iter);
+                s_dec = stop;
+                if (stop && b == 0) {
+                    P.st->iters = s - 1;
+                    P.st->err = ed;
+                    P.st->converged = (ed <= P.tol);
+                }
+            }
+        }
+        {
+            const double* Gold = P.G + ((s - 1) & 1) * Jp;
+            double* Gnew = P.G + (s & 1) * Jp;
+            const int gw = b * (NCW - 1) + (warp - 1), nw = nb * (NCW - 1);
+            for (int j = gw; warp > 0 && j < J; j += nw) {
+                float2 sum = make_float2(0.f, 0.f);
+                for (int bb = lane; bb < nb; bb += 32) sum = df_add(sum, P.colpart[(int64_t)bb * Jp + j]);
+                sum = warp_sum_df(sum);
+                if (lane == 0) {
+                    if (!(sum.x > 0.f) || !isfinite(sum.x)) {
+                        atomicCAS(status, DEV_OK, DEV_ENUMERIC);
+                    } else {
+                        const float2 ls = df_log2(sum);  // log2 s_j = ls.x + ls.y
+                        const float Gu = (float)Gold[j];
+                        Gnew[j] = ((double)Gu - (double)ls.x) + (LQ[j] - (double)ls.y);
+                    }
+                }
+            }
+        }
+        bar_named(CONS_BAR, NC);
+        if (s_dec) {
+            for (int r = tid; r < nrow; r += NC) P.F_out[r0 + r] = Fold[r];
+            if (tid == 0) s_stop = 1;
+            return;
+        }
+        OTA_BARRIER();
+        load_G_smem(P.G + (s & 1) * Jp, J, Jp, Gs, tid, NC);
+        bar_named(CONS_BAR, NC);
+    }
+#undef OTA_BARRIER
 }
 
 // ------------------------------------------------------------------------------------------
 // Finalize: plan, potentials in natural units, FP64 reductions of marginals, cost and loads.
-// One team of NT_F threads per row; per-thread column accumulators in FP64.
+// Each CTA walks its rows RB at a time; thread t owns the column chunks t, t + NT_F, ...
+// (few columns per thread, so FP64 column accumulators are cheap).  Each thread sums its
+// few cells of a row in FP32, the warp reduces those with error-free two-sums, warps are
+// combined in FP64; column sums over a block of rows go from FP32 into the FP64
+// accumulators.
 // ------------------------------------------------------------------------------------------
 struct FinParams {
     const float* C;
@@ -403,86 +719,168 @@ struct FinParams {
     int Jp;
     const float* p;
     const DevScalars* sc;
-    const double* F0;
-    const double* F1;
     const LoopState* st;
+    const float2* F;
     const double* G;
     float k_hi, k_lo;
     double eps_ln2;
     float* pi;
     int64_t pi_ld;
     double* f_out;
-    double2* fpart;   // [nb][Jp] (sum p^ t, sum p^ C t)
-    double* epart;    // [nb][2] (row residual, cost)
+    double2* fpart;  // [nb][Jp] (sum p^ t, sum p^ C t)
+    double* epart;   // [nb] row residual
 };
 
-template <int VPT>
-__global__ void __launch_bounds__(NT_F) sk_finalize(FinParams P) {
-    constexpr int TW = NT_F / 32;
-    __shared__ double redd[2 * TW];
+// Sum of (s, e) pairs over a warp with error-free additions.
+__device__ __forceinline__ void warp_sum_pair(float& s, float& e) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+        float t, u;
+        two_sum(s, s2, t, u);
+        s = t;
+        e = e + e2 + u;
+    }
+}
+
+// Warp-per-row teams as in the solver.  Each lane keeps FP32 column sums of p^ t and
+// p^ C t for FIN_FLUSH rows, then adds them into its team's FP64 accumulators in shared
+// memory (each lane owns its columns: no conflicts); CTAs add their teams in team order.
+// The next row is loaded while the current one is worked on.
+static constexpr int FIN_FLUSH = 16;
+
+template <int TW, int VPT>
+__global__ void __launch_bounds__(NT_F, 1) sk_finalize(FinParams P) {
+    constexpr int TT = 32 * TW, NTEAMS = NT_F / TT;
+    extern __shared__ __align__(16) float4 accs[];  // [NTEAMS][Jp]: (sum p^ t, sum p^ C t) as pairs
+    __shared__ float red[2 * NTEAMS * TW * 2];
+    __shared__ float errs[NTEAMS];
+    if (P.st->status != DEV_OK) return;
     const Team<TW> tm;
-    if (P.sc->status != DEV_OK || P.st->status != DEV_OK) return;
-    const int J = P.J;
+    const int J = P.J, Jp = P.Jp;
     const int nb = gridDim.x, b = blockIdx.x;
     const int64_t r0 = P.I * b / nb, r1 = P.I * (b + 1) / nb;
-    const double* __restrict__ F = (P.st->iters & 1) ? P.F1 : P.F0;
+    const double* Gk = P.G + (P.st->iters & 1) * Jp;  // G^k of the returned plan
+    for (int q = threadIdx.x; q < NTEAMS * Jp; q += NT_F) accs[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    float4* myacc = accs + (size_t)tm.team * Jp;
     float4 g[VPT];
-    load_G<TW, VPT>(P.G, J, tm.tl, g);
-    double apI[VPT * 4], arho[VPT * 4];
 #pragma unroll
-    for (int k = 0; k < VPT * 4; ++k) apI[k] = arho[k] = 0.0;
-    double errt = 0.0, costt = 0.0;
-    int par = 0;
-    for (int64_t i = r0; i < r1; ++i) {
+    for (int v = 0; v < VPT; ++v) {
+        const int col = 4 * (tm.tl + TT * v);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) comp(g[v], c) = (col + c < J) ? (float)Gk[col + c] : 0.0f;
+    }
+    const float inv_sp_f = P.sc->inv_sp_f;
+    float cpi[VPT * 4], crho[VPT * 4];
+#pragma unroll
+    for (int q = 0; q < VPT * 4; ++q) cpi[q] = crho[q] = 0.f;
+    float errt = 0.f;
+    int par = 0, since = 0;
+    int64_t i = r0 + tm.team;
+    float4 xn[VPT];
+    if (i < r1) load_row<TW, VPT>(P.C + i * P.ld, J, tm.tl, xn);
+    for (; i < r1; i += NTEAMS) {
         float4 x[VPT];
-        load_row<TW, VPT>(P.C + i * P.ld, J, tm.tl, x);
-        const double Fd = F[i];
-        float Fh, Fl;
-        split_f(Fd, &Fh, &Fl);
-        const float pi_ = __ldg(P.p + i);
-        const double ph = (double)pi_ * P.sc->inv_sp;
-        float rs = 0.f, cs = 0.f;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) x[v] = xn[v];
+        const int64_t inext = i + NTEAMS;
+        if (inext < r1) load_row<TW, VPT>(P.C + inext * P.ld, J, tm.tl, xn);
+        const float2 F = P.F[i];
+        const float pf = __ldg(P.p + i);  // f_i itself is formed by sk_finalize_cols (all lanes busy)
+        const float phf = pf * inv_sp_f;
+        float rs = 0.f;
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
-            const int col = 4 * (tm.tl + NT_F * v);
+            const int col = 4 * (tm.tl + TT * v);
+            if (col < J) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float cost = comp(x[v], c);
-                const float t = ex2(expo(Fh, Fl + comp(g[v], c), cost, P.k_hi, P.k_lo));
-                const float ct = t > 0.f ? cost * t : 0.f;
-                rs += t;
-                cs += ct;
-                apI[v * 4 + c] = fma(ph, (double)t, apI[v * 4 + c]);
-                arho[v * 4 + c] = fma(ph, (double)ct, arho[v * 4 + c]);
-                if (P.pi && col + c < J) P.pi[i * P.pi_ld + col + c] = pi_ * t;
+                for (int c = 0; c < 4; ++c) {
+                    const float cost = comp(x[v], c);
+                    const float t = ex2(expo(F.x, F.y + comp(g[v], c), cost, P.k_hi, P.k_lo));
+                    const float ct = t > 0.f ? cost * t : 0.f;
+                    rs += t;
+                    cpi[v * 4 + c] = fmaf(phf, t, cpi[v * 4 + c]);
+                    crho[v * 4 + c] = fmaf(phf, ct, crho[v * 4 + c]);
+                    if (P.pi && col + c < J) P.pi[i * P.pi_ld + col + c] = pf * t;
+                }
             }
         }
-        const double rsd = team_reduce<TW, double, false>((double)rs, redd, 1, tm, par);
-        const double csd = team_reduce<TW, double, false>((double)cs, redd, 1, tm, par);
-        if (tm.tl == 0) {
-            errt += ph * fabs(rsd - 1.0);
-            costt += ph * csd;
-            P.f_out[i] = P.eps_ln2 * (Fd + log2((double)pi_));
+        // error-free team sum of the row: warp pairs, then the team's warps in order
+        float se = 0.f;
+        warp_sum_pair(rs, se);
+        if constexpr (TW > 1) {
+            float2* r = reinterpret_cast<float2*>(red) + (par * NTEAMS + tm.team) * TW;
+            if (tm.lane == 0) r[tm.wit] = make_float2(rs, se);
+            bar_named(1 + tm.team, TT);
+            float2 a = r[0];
+            for (int w = 1; w < TW; ++w) a = df_add2(a, r[w]);
+            par ^= 1;
+            rs = a.x;
+            se = a.y;
+        }
+        // |row sum - 1| in FP32: rs - 1 is exact near 1, the pair's low part is added after
+        errt = fmaf(phf, fabsf((rs - 1.0f) + se), errt);
+        if (++since == FIN_FLUSH) {
+            since = 0;
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int col = 4 * (tm.tl + TT * v);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (col + c < J) {
+                        float4 a = myacc[col + c];
+                        const float2 s2 = df_add(make_float2(a.x, a.y), cpi[v * 4 + c]);
+                        const float2 r2 = df_add(make_float2(a.z, a.w), crho[v * 4 + c]);
+                        myacc[col + c] = make_float4(s2.x, s2.y, r2.x, r2.y);
+                        cpi[v * 4 + c] = crho[v * 4 + c] = 0.f;
+                    }
+            }
         }
     }
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-        const int col = 4 * (tm.tl + NT_F * v);
+        const int col = 4 * (tm.tl + TT * v);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (col + c < J) P.fpart[(int64_t)b * P.Jp + col + c] = make_double2(apI[v * 4 + c], arho[v * 4 + c]);
+            if (col + c < J) {
+                float4 a = myacc[col + c];
+                const float2 s2 = df_add(make_float2(a.x, a.y), cpi[v * 4 + c]);
+                const float2 r2 = df_add(make_float2(a.z, a.w), crho[v * 4 + c]);
+                myacc[col + c] = make_float4(s2.x, s2.y, r2.x, r2.y);
+            }
+    }
+    if (tm.tl == 0) errs[tm.team] = errt;
+    __syncthreads();
+    for (int j = threadIdx.x; j < J; j += NT_F) {
+        float4 a = accs[j];
+        float2 s = make_float2(a.x, a.y), r = make_float2(a.z, a.w);
+        for (int t = 1; t < NTEAMS; ++t) {
+            const float4 o = accs[(size_t)t * Jp + j];
+            s = df_add2(s, make_float2(o.x, o.y));
+            r = df_add2(r, make_float2(o.z, o.w));
+        }
+        P.fpart[(int64_t)b * Jp + j] = make_double2((double)s.x + (double)s.y, (double)r.x + (double)r.y);
     }
     if (threadIdx.x == 0) {
-        P.epart[2 * b] = errt;
-        P.epart[2 * b + 1] = costt;
+        float2 e = make_float2(errs[0], 0.f);
+        for (int t = 1; t < NTEAMS; ++t) e = df_add(e, errs[t]);
+        P.epart[b] = (double)e.x + (double)e.y;
     }
 }
 
 __global__ void sk_finalize_cols(const double2* __restrict__ fpart, int nb, int Jp, int J,
                                  const float* __restrict__ q, const DevScalars* sc,
-                                 const LoopState* st, const double* __restrict__ G, double eps_ln2,
-                                 double* g_out, double* rrh_load, double* colerr) {
-    if (sc->status != DEV_OK || st->status != DEV_OK) return;
+                                 const LoopState* st, const double* G, double eps_ln2,
+                                 double* g_out, double* rrh_load, double2* cols, const float2* __restrict__ F,
+                                 const float* __restrict__ p, int64_t I, double* f_out) {
+    if (st->status != DEV_OK) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 Fi = F[i];
+        f_out[i] = eps_ln2 * ((double)Fi.x + (double)Fi.y + log2((double)p[i]));
+    }
+    G += (st->iters & 1) * Jp;  // G^k of the returned plan
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -496,24 +894,26 @@ __global__ void sk_finalize_cols(const double2* __restrict__ fpart, int nb, int 
         s = warp_sum(s);
         r = warp_sum(r);
         if (lane == 0) {
-            colerr[j] = fabs(s - (double)q[j] * sc->inv_sq);
+            cols[j] = make_double2(fabs(s - (double)q[j] * sc->inv_sq), r);
             if (rrh_load) rrh_load[j] = r * sc->sp;
             g_out[j] = eps_ln2 * G[j];
         }
     }
 }
 
-__global__ void sk_summary(const double* __restrict__ epart, int nb, const double* __restrict__ colerr,
-                           int J, const DevScalars* sc, const LoopState* st, SolveSummary* out) {
+// Totals: row residual (per-CTA partials), column residual and transport cost = sum_j rho_j.
+__global__ void sk_summary(const double* __restrict__ epart, int nb, const double2* __restrict__ cols, int J,
+                           const DevScalars* sc, const LoopState* st, SolveSummary* out) {
     __shared__ double sh[3][32];
     double er = 0.0, co = 0.0, ec = 0.0;
-    const bool ok = sc->status == DEV_OK && st->status == DEV_OK;
+    const bool ok = st->status == DEV_OK;
     if (ok) {
-        for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) {
-            er += epart[2 * bb];
-            co += epart[2 * bb + 1];
+        for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) er += epart[bb];
+        for (int j = threadIdx.x; j < J; j += blockDim.x) {
+            const double2 c = cols[j];
+            ec += c.x;
+            co += c.y;
         }
-        for (int j = threadIdx.x; j < J; j += blockDim.x) ec += colerr[j];
     }
     er = warp_sum(er);
     co = warp_sum(co);
@@ -533,36 +933,41 @@ __global__ void sk_summary(const double* __restrict__ epart, int nb, const doubl
         }
         out->err_row = a;
         out->err_col = e;
-        out->cost = c * sc->sp;
+        out->cost = ok ? c * sc->sp : 0.0;
         out->err_loop = st->err;
         out->iters = st->iters;
         out->converged = st->converged;
-        out->status = sc->status != DEV_OK ? sc->status : st->status;
+        out->status = st->status;
         out->absorptions = 0;
     }
 }
 
 // ------------------------------------------------------------------------------------------
-// Host launcher.
+// Host side.
 // ------------------------------------------------------------------------------------------
 namespace {
 
 struct Kernels {
-    const void* init_rows;
-    const void* loop;
-    int tw, vpt;
+    const void* solve;
+    const void* fin;
+    int tw, vpt, ncw;
 };
 
 template <int TW, int VPT>
 Kernels kernels_for() {
-    return Kernels{(const void*)sk_init_rows<TW, VPT>, (const void*)sk_loop<TW, VPT>, TW, VPT};
+    return Kernels{(const void*)sk_solve<TW, VPT>, (const void*)sk_finalize<TW, VPT>, TW, VPT, Cons<TW>::NCW};
 }
 
+// One-warp teams (TW = 1) get VPT = ceil(J4 / 32) exactly; chunk_inside() relies on it.
 bool pick_kernels(int J, Kernels* k) {
     const int J4 = (J + 3) / 4;
     if (J4 <= 32) *k = kernels_for<1, 1>();
     else if (J4 <= 64) *k = kernels_for<1, 2>();
+    else if (J4 <= 96) *k = kernels_for<1, 3>();
     else if (J4 <= 128) *k = kernels_for<1, 4>();
+    else if (J4 <= 160) *k = kernels_for<1, 5>();
+    else if (J4 <= 192) *k = kernels_for<1, 6>();
+    else if (J4 <= 224) *k = kernels_for<1, 7>();
     else if (J4 <= 256) *k = kernels_for<1, 8>();
     else if (J4 <= 512) *k = kernels_for<2, 8>();
     else if (J4 <= 1024) *k = kernels_for<4, 8>();
@@ -571,12 +976,160 @@ bool pick_kernels(int J, Kernels* k) {
     return true;
 }
 
-const void* pick_finalize(int J) {
-    const int J4 = (J + 3) / 4;
-    if (J4 <= NT_F) return (const void*)sk_finalize<1>;
-    if (J4 <= 2 * NT_F) return (const void*)sk_finalize<2>;
-    if (J4 <= 4 * NT_F) return (const void*)sk_finalize<4>;
-    return nullptr;
+// Finalize launch: one CTA per SM (the team accumulators take most of the shared memory).
+ot_status plan_finalize(const Kernels& kk, int64_t I, int Jp, int num_sms, int cap, int* grid, size_t* smem) {
+    const int nteams = NT_F / (32 * kk.tw);
+    *smem = (size_t)nteams * Jp * sizeof(float4);
+    if (*smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kk.fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem) != cudaSuccess) {
+        cudaGetLastError();
+        return OT_ECUDA;
+    }
+    *grid = (int)std::max<int64_t>(1, std::min<int64_t>({(I + nteams - 1) / nteams, (int64_t)num_sms, (int64_t)cap}));
+    return OT_OK;
+}
+
+// Stage geometry, shared-memory layout and grid of the persistent kernel.
+struct LoopLaunch {
+    StreamCfg cfg;
+    size_t smem;
+    int grid;
+};
+
+ot_status plan_solve(const Kernels& kk, int64_t I, int Jp, int64_t ld, int num_sms, int cap, LoopLaunch* L) {
+    const int nteams = kk.ncw / kk.tw;
+    const size_t comb = (size_t)((nteams + 1) / 2) * Jp * sizeof(float);
+    const size_t row_bytes = (size_t)ld * sizeof(float);
+    const size_t budget = 232448 - 2048;  // 227 KB per block minus static shared memory
+    int rpt = (int)std::max<size_t>(1, 24576 / ((size_t)nteams * row_bytes));
+    bool planned = false;
+    while (!planned) {
+        const int rs = nteams * rpt;
+        const int64_t blocks = (I + rs - 1) / rs;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>({blocks, (int64_t)num_sms, (int64_t)cap}));
+        const int64_t bpc = (blocks + grid - 1) / grid;  // most blocks any CTA owns
+        const int rmax = (int)std::min<int64_t>(bpc * rs, I);
+        const size_t off_G = round_up(SMEM_HDR + comb, 16);
+        const size_t off_F = round_up(off_G + (size_t)Jp * sizeof(float), 16);
+        const size_t off_P = off_F + (size_t)2 * rmax * sizeof(float2);
+        const size_t off_ring = round_up(off_P + (size_t)rmax * sizeof(float), 128);
+        const size_t stage = (size_t)rs * row_bytes;
+        const int stages = off_ring < budget ? (int)std::min<size_t>(MAX_STAGES, (budget - off_ring) / stage) : 0;
+        if (stages >= 3 || (stages >= 2 && rpt == 1)) {
+            L->cfg.rpt = rpt;
+            L->cfg.rows_per_stage = rs;
+            L->cfg.stages = stages;
+            L->cfg.stage_floats = (int)(stage / sizeof(float));
+            L->cfg.rmax = rmax;
+            L->cfg.off_G = (int)off_G;
+            L->cfg.off_F = (int)off_F;
+            L->cfg.off_P = (int)off_P;
+            L->cfg.off_ring = (int)off_ring;
+            L->smem = off_ring + (size_t)stages * stage;
+            L->grid = grid;
+            planned = true;
+        } else if (rpt == 1) {
+            return OT_EUNSUPPORTED;  // the rows a CTA owns do not fit next to two stages
+        } else {
+            rpt = std::max(1, rpt / 2);
+        }
+    }
+    if (cudaFuncSetAttribute(kk.solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem) != cudaSuccess) {
+        cudaGetLastError();
+        return OT_ECUDA;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk.solve, 32 * (kk.ncw + 1), L->smem) != cudaSuccess) {
+        cudaGetLastError();
+        return OT_ECUDA;
+    }
+    if (occ < 1 || L->grid > occ * num_sms) return OT_EUNSUPPORTED;  // cooperative launch: all co-resident
+    return OT_OK;
+}
+
+// Device buffers of one solve.
+struct SolveBufs {
+    DevScalars* sc;
+    LoopState* ls;
+    SolveSummary* summ;
+    double2* cols;
+    double* G;
+    double* errpart;
+    void* colpart;
+    float2* F;
+};
+
+// Enqueue the whole solve; the caller copies B.summ back.
+cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunch& LL, int nb_fin, size_t smem_fin,
+                          const SolveBufs& B, long long spin, cudaStream_t s, ot_assoc_ctx* ctx) {
+    const int J = a.J;
+    const int64_t I = a.I;
+    const int Jp = (int)round_up(J, 4);
+    const double k = LOG2E / a.eps;
+    float k_hi, k_lo;
+    split_k(k, &k_hi, &k_lo);
+    if (ctx) timing_mark(ctx, 0, s);
+    cudaError_t e = cudaMemsetAsync(B.sc, 0, 1024, s);  // DevScalars, LoopState, summary
+    if (e != cudaSuccess) return e;
+    SolveParams P;
+    P.C = a.C;
+    P.ld = a.ld;
+    P.I = I;
+    P.J = J;
+    P.Jp = Jp;
+    P.p = a.p;
+    P.q = a.q;
+    P.g_warm = a.warm_start ? a.out->g : nullptr;
+    P.input_bad = a.input_bad;
+    P.sc = B.sc;
+    P.st = B.ls;
+    P.G = B.G;
+    P.F_out = B.F;
+    P.colpart = (float*)B.colpart;
+    P.errpart = B.errpart;
+    P.k = k;
+    P.k_hi = k_hi;
+    P.k_lo = k_lo;
+    P.tol = a.tol;
+    P.max_iter = a.max_iter;
+    P.spin = spin;
+    if (ctx) timing_mark(ctx, 1, s);
+    {
+        void* args[] = {&P, (void*)&LL.cfg};
+        e = cudaLaunchCooperativeKernel(kk.solve, dim3(LL.grid), dim3(32 * (kk.ncw + 1)), args, LL.smem, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (ctx) timing_mark(ctx, 2, s);
+    FinParams Q;
+    Q.C = a.C;
+    Q.ld = a.ld;
+    Q.I = I;
+    Q.J = J;
+    Q.Jp = Jp;
+    Q.p = a.p;
+    Q.sc = B.sc;
+    Q.st = B.ls;
+    Q.F = B.F;
+    Q.G = B.G;
+    Q.k_hi = k_hi;
+    Q.k_lo = k_lo;
+    Q.eps_ln2 = a.eps * LN2;
+    Q.pi = a.out->pi;
+    Q.pi_ld = a.out->pi_ld > 0 ? a.out->pi_ld : J;
+    Q.f_out = a.out->f;
+    Q.fpart = (double2*)B.colpart;
+    Q.epart = B.errpart;
+    {
+        void* args[] = {&Q};
+        e = cudaLaunchKernel(kk.fin, dim3(nb_fin), dim3(NT_F), args, smem_fin, s);
+        if (e != cudaSuccess) return e;
+    }
+    const int nb_cols = (int)std::max<int64_t>((J + 15) / 16, std::min<int64_t>((I + 511) / 512, 1024));
+    sk_finalize_cols<<<nb_cols, 512, 0, s>>>((const double2*)B.colpart, nb_fin, Jp, J, a.q, B.sc, B.ls, B.G,
+                                             a.eps * LN2, a.out->g, a.out->rrh_load, B.cols, B.F, a.p, I, a.out->f);
+    sk_summary<<<1, 256, 0, s>>>(B.errpart, nb_fin, B.cols, J, B.sc, B.ls, B.summ);
+    if (ctx) timing_mark(ctx, 3, s);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -587,133 +1140,38 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
     const int64_t I = a.I;
     const int Jp = (int)round_up(J, 4);
     Kernels kk;
-    const void* kfin = pick_finalize(J);
-    if (!pick_kernels(J, &kk) || !kfin) return set_error(ctx, OT_EUNSUPPORTED, "J=%d above 8192", J);
-    const int nteams = NT / (32 * kk.tw);
-    cudaError_t e;
-
-    // Grid sizes.
-    const size_t smem_loop = (size_t)nteams * Jp * sizeof(float);
-    const size_t smem_init = (size_t)nteams * Jp * sizeof(float2);
-    for (const void* fn : {kk.loop, kk.init_rows}) {
-        const size_t sm = fn == kk.loop ? smem_loop : smem_init;
-        if (sm > 48 * 1024) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return cuda_error(ctx, e, "cudaFuncSetAttribute");
-        }
-    }
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk.loop, NT, smem_loop);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "occupancy");
-    if (occ < 1) return set_error(ctx, OT_EUNSUPPORTED, "solver kernel does not fit on an SM");
-    const int64_t rows_per_team_min = 8;
-    int64_t want = (I + (int64_t)nteams * rows_per_team_min - 1) / ((int64_t)nteams * rows_per_team_min);
-    const int nb_loop = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)occ * ctx->num_sms));
-    int occ_i = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_i, kk.init_rows, NT, smem_init);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "occupancy");
-    const int nb_init = (int)std::max<int64_t>(
-        1, std::min<int64_t>((I + nteams - 1) / nteams, (int64_t)std::max(occ_i, 1) * ctx->num_sms));
-    const int nb_fin = (int)std::max<int64_t>(1, std::min<int64_t>(I, (int64_t)4 * ctx->num_sms));
-    const int nb_part = std::max(std::max(nb_loop, nb_init), nb_fin);
-
-    // Scratch.
-    double* F = (double*)scratch(ctx, SLOT_F, sizeof(double) * 2 * (size_t)I, &st);
+    if (!pick_kernels(J, &kk)) return set_error(ctx, OT_EUNSUPPORTED, "J=%d above 8192", J);
+    LoopLaunch LL;
+    st = plan_solve(kk, I, Jp, a.ld, ctx->num_sms, 1 << 30, &LL);
+    if (st) return set_error(ctx, st, "solver does not fit the shared memory (I=%lld J=%d)", (long long)I, J);
+    int nb_fin = 1;
+    size_t smem_fin = 0;
+    st = plan_finalize(kk, I, Jp, ctx->num_sms, 1 << 30, &nb_fin, &smem_fin);
+    if (st) return set_error(ctx, st, "finalize launch setup failed");
+    const int nb_part = std::max(LL.grid, nb_fin);
+    SolveBufs B;
+    B.F = (float2*)scratch(ctx, SLOT_F, sizeof(float2) * (size_t)I, &st);
     if (st) return st;
-    double* G = (double*)scratch(ctx, SLOT_G, sizeof(double) * (size_t)Jp, &st);
+    B.G = (double*)scratch(ctx, SLOT_G, sizeof(double) * 3 * (size_t)Jp, &st);
     if (st) return st;
-    void* colpart = scratch(ctx, SLOT_COLPART, sizeof(double2) * (size_t)nb_part * Jp, &st);
+    B.colpart = scratch(ctx, SLOT_COLPART, sizeof(double2) * (size_t)nb_part * Jp, &st);
     if (st) return st;
-    double* errpart = (double*)scratch(ctx, SLOT_ERRPART, sizeof(double) * 2 * (size_t)nb_part, &st);
+    B.errpart = (double*)scratch(ctx, SLOT_ERRPART, sizeof(double) * 2 * (size_t)nb_part, &st);
     if (st) return st;
-    char* state = (char*)scratch(ctx, SLOT_STATE, 4096 + sizeof(double) * (size_t)Jp, &st);
+    char* state = (char*)scratch(ctx, SLOT_STATE, 4096 + sizeof(double2) * (size_t)Jp, &st);
     if (st) return st;
-    DevScalars* sc = (DevScalars*)state;
-    LoopState* ls = (LoopState*)(state + 256);
-    SolveSummary* summ = (SolveSummary*)(state + 512);
-    double* colerr = (double*)(state + 4096);
+    B.sc = (DevScalars*)state;
+    B.ls = (LoopState*)(state + 256);
+    B.summ = (SolveSummary*)(state + 512);
+    B.cols = (double2*)(state + 4096);
     SolveSummary* hsum = (SolveSummary*)host_staging(ctx, sizeof(SolveSummary), &st);
     if (st) return st;
-
-    const double k = LOG2E / a.eps;
-    float k_hi, k_lo;
-    split_k(k, &k_hi, &k_lo);
-    cudaStream_t s = a.stream;
-
     ctx->last_timings.valid = 0;
-    timing_mark(ctx, 0, s);
-    e = cudaMemsetAsync(state, 0, 1024, s);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "memset");
-    sk_prep<<<1, 1024, 0, s>>>(a.p, a.q, I, J, a.warm_start ? a.out->g : nullptr, k, a.input_bad, sc, G);
-    {
-        double* F1 = F + I;
-        void* args[] = {(void*)&a.C, (void*)&a.ld, (void*)&I,       (void*)&J,
-                        (void*)&Jp,  (void*)&a.p,  (void*)&sc,      (void*)&G,
-                        (void*)&F1,  &colpart,     (void*)&k_hi,    (void*)&k_lo};
-        e = cudaLaunchKernel(kk.init_rows, dim3(nb_init), dim3(NT), args, smem_init, s);
-        if (e != cudaSuccess) return cuda_error(ctx, e, "init_rows launch");
-    }
-    sk_init_cols<<<(J + 7) / 8, 256, 0, s>>>((const float2*)colpart, nb_init, Jp, J, a.q, sc, G);
-
-    LoopParams P;
-    P.C = a.C;
-    P.ld = a.ld;
-    P.I = I;
-    P.J = J;
-    P.Jp = Jp;
-    P.p = a.p;
-    P.q = a.q;
-    P.sc = sc;
-    P.F0 = F;
-    P.F1 = F + I;
-    P.G = G;
-    P.colpart = (float*)colpart;
-    P.errpart = errpart;
-    P.st = ls;
-    P.k_hi = k_hi;
-    P.k_lo = k_lo;
-    P.tol = a.tol;
-    P.max_iter = a.max_iter;
-    P.spin = ctx->spin_limit;
-    timing_mark(ctx, 1, s);
-    {
-        void* args[] = {&P};
-        e = cudaLaunchCooperativeKernel(kk.loop, dim3(nb_loop), dim3(NT), args, smem_loop, s);
-        if (e != cudaSuccess) return cuda_error(ctx, e, "cooperative solver launch");
-    }
-    timing_mark(ctx, 2, s);
-
-    FinParams Q;
-    Q.C = a.C;
-    Q.ld = a.ld;
-    Q.I = I;
-    Q.J = J;
-    Q.Jp = Jp;
-    Q.p = a.p;
-    Q.sc = sc;
-    Q.F0 = F;
-    Q.F1 = F + I;
-    Q.st = ls;
-    Q.G = G;
-    Q.k_hi = k_hi;
-    Q.k_lo = k_lo;
-    Q.eps_ln2 = a.eps * LN2;
-    Q.pi = a.out->pi;
-    Q.pi_ld = a.out->pi_ld > 0 ? a.out->pi_ld : J;
-    Q.f_out = a.out->f;
-    Q.fpart = (double2*)colpart;
-    Q.epart = errpart;
-    {
-        void* args[] = {&Q};
-        e = cudaLaunchKernel(kfin, dim3(nb_fin), dim3(NT_F), args, 0, s);
-        if (e != cudaSuccess) return cuda_error(ctx, e, "finalize launch");
-    }
-    sk_finalize_cols<<<(J + 15) / 16, 512, 0, s>>>((const double2*)colpart, nb_fin, Jp, J, a.q, sc, ls, G,
-                                                   a.eps * LN2, a.out->g, a.out->rrh_load, colerr);
-    sk_summary<<<1, 256, 0, s>>>(errpart, nb_fin, colerr, J, sc, ls, summ);
-    timing_mark(ctx, 3, s);
-    ctx->launches += 8;
-    e = cudaMemcpyAsync(hsum, summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, s);
+    cudaStream_t s = a.stream;
+    cudaError_t e = enqueue_solve(a, kk, LL, nb_fin, smem_fin, B, ctx->spin_limit, s, ctx);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "solve launch");
+    ctx->launches += 4;
+    e = cudaMemcpyAsync(hsum, B.summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_error(ctx, e, "summary copy");
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(ctx, e, "solve");
@@ -721,8 +1179,6 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
     timing_collect(ctx, hsum->iters);
     return OT_OK;
 }
-
-}  // namespace ota
 
 // ------------------------------------------------------------------------------------------
 // Solve without any allocation: the same kernels as launch_solve_f32, with every scratch
@@ -734,8 +1190,6 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
 // under a fixed memory pool and has no room to grow one.  The array is part of the loaded
 // library image: every GPU that loads the library holds NOALLOC_BYTES of it until exit.
 // ------------------------------------------------------------------------------------------
-namespace ota {
-
 static constexpr size_t NOALLOC_BYTES = size_t(8) << 20;  // 8 MiB
 static constexpr int64_t NOALLOC_MAX_I = 131072;
 static constexpr int NOALLOC_MAX_J = 1024;
@@ -744,13 +1198,13 @@ static constexpr int NOALLOC_MAX_CTAS = 320;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 // Byte offsets inside g_noalloc_scratch (all multiples of 256).
-static constexpr size_t NA_STATE = 0;                                    // DevScalars/LoopState/summary
-static constexpr size_t NA_COLERR = 4096;                                // Jp doubles
-static constexpr size_t NA_G = NA_COLERR + 8 * NOALLOC_MAX_J;            // Jp doubles
-static constexpr size_t NA_ERRPART = NA_G + 8 * NOALLOC_MAX_J;           // 2 * CTAs doubles
-static constexpr size_t NA_COLPART = NA_ERRPART + 16 * NOALLOC_MAX_CTAS; // CTAs * Jp double2
+static constexpr size_t NA_STATE = 0;                                     // DevScalars/LoopState/summary
+static constexpr size_t NA_COLS = 4096;                                   // Jp double2
+static constexpr size_t NA_G = NA_COLS + 16 * NOALLOC_MAX_J;              // 3 * Jp doubles
+static constexpr size_t NA_ERRPART = NA_G + 24 * NOALLOC_MAX_J;           // 2 * CTAs doubles
+static constexpr size_t NA_COLPART = NA_ERRPART + 16 * NOALLOC_MAX_CTAS;  // CTAs * Jp double2
 static constexpr size_t NA_F = NA_COLPART + 16 * (size_t)NOALLOC_MAX_CTAS * NOALLOC_MAX_J;
-static constexpr size_t NA_END = NA_F + 16 * (size_t)NOALLOC_MAX_I;      // 2 * I doubles
+static constexpr size_t NA_END = NA_F + 16 * (size_t)NOALLOC_MAX_I;       // I float2 (+ room)
 static_assert(NA_END <= NOALLOC_BYTES, "no-allocation scratch layout does not fit");
 static_assert(NA_COLPART % 256 == 0 && NA_F % 256 == 0, "alignment");
 
@@ -788,117 +1242,29 @@ static ot_status noalloc_solve(const SolveArgs& a, SolveSummary* sum_host) {
     ot_status st = noalloc_base(dev, &base);
     if (st) return st;
     Kernels kk;
-    const void* kfin = pick_finalize(J);
-    if (!pick_kernels(J, &kk) || !kfin) return OT_EUNSUPPORTED;
-    const int nteams = NT / (32 * kk.tw);
-    const size_t smem_loop = (size_t)nteams * Jp * sizeof(float);
-    const size_t smem_init = (size_t)nteams * Jp * sizeof(float2);
-    cudaError_t e;
-    for (const void* fn : {kk.loop, kk.init_rows}) {
-        const size_t sm = fn == kk.loop ? smem_loop : smem_init;
-        if (sm > 48 * 1024 &&
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
-            cudaGetLastError();
-            return OT_ECUDA;
-        }
-    }
-    int occ = 0, occ_i = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk.loop, NT, smem_loop) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_i, kk.init_rows, NT, smem_init) != cudaSuccess) {
-        cudaGetLastError();
-        return OT_ECUDA;
-    }
-    if (occ < 1) return OT_EUNSUPPORTED;
-    const int64_t cap = NOALLOC_MAX_CTAS;
-    const int64_t want = (I + (int64_t)nteams * 8 - 1) / ((int64_t)nteams * 8);
-    const int nb_loop = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)occ * nsm, cap}));
-    const int nb_init = (int)std::max<int64_t>(
-        1, std::min<int64_t>({(I + nteams - 1) / nteams, (int64_t)std::max(occ_i, 1) * nsm, cap}));
-    const int nb_fin = (int)std::max<int64_t>(1, std::min<int64_t>({I, (int64_t)4 * nsm, cap}));
-
+    if (!pick_kernels(J, &kk)) return OT_EUNSUPPORTED;
+    LoopLaunch LL;
+    st = plan_solve(kk, I, Jp, a.ld, nsm, NOALLOC_MAX_CTAS, &LL);
+    if (st) return st;
+    int nb_fin = 1;
+    size_t smem_fin = 0;
+    st = plan_finalize(kk, I, Jp, nsm, NOALLOC_MAX_CTAS, &nb_fin, &smem_fin);
+    if (st) return st;
+    SolveBufs B;
     char* state = (char*)(base + NA_STATE);
-    DevScalars* sc = (DevScalars*)state;
-    LoopState* ls = (LoopState*)(state + 256);
-    SolveSummary* summ = (SolveSummary*)(state + 512);
-    double* colerr = (double*)(base + NA_COLERR);
-    double* G = (double*)(base + NA_G);
-    double* errpart = (double*)(base + NA_ERRPART);
-    void* colpart = (void*)(base + NA_COLPART);
-    double* F = (double*)(base + NA_F);
-
-    const double k = LOG2E / a.eps;
-    float k_hi, k_lo;
-    split_k(k, &k_hi, &k_lo);
-    cudaStream_t s = a.stream;
-    // The state words must start at zero on every call (the array keeps the last call's data).
-    e = cudaMemsetAsync(state, 0, 1024, s);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return OT_ECUDA;
-    }
-    sk_prep<<<1, 1024, 0, s>>>(a.p, a.q, I, J, a.warm_start ? a.out->g : nullptr, k, nullptr, sc, G);
-    {
-        double* F1 = F + I;
-        void* args[] = {(void*)&a.C, (void*)&a.ld, (void*)&I,    (void*)&J,  (void*)&Jp,   (void*)&a.p,
-                        (void*)&sc,  (void*)&G,    (void*)&F1,   &colpart,   (void*)&k_hi, (void*)&k_lo};
-        e = cudaLaunchKernel(kk.init_rows, dim3(nb_init), dim3(NT), args, smem_init, s);
-    }
-    if (e == cudaSuccess) {
-        sk_init_cols<<<(J + 7) / 8, 256, 0, s>>>((const float2*)colpart, nb_init, Jp, J, a.q, sc, G);
-        LoopParams P;
-        P.C = a.C;
-        P.ld = a.ld;
-        P.I = I;
-        P.J = J;
-        P.Jp = Jp;
-        P.p = a.p;
-        P.q = a.q;
-        P.sc = sc;
-        P.F0 = F;
-        P.F1 = F + I;
-        P.G = G;
-        P.colpart = (float*)colpart;
-        P.errpart = errpart;
-        P.st = ls;
-        P.k_hi = k_hi;
-        P.k_lo = k_lo;
-        P.tol = a.tol;
-        P.max_iter = a.max_iter;
-        P.spin = 1LL << 24;
-        void* args[] = {&P};
-        e = cudaLaunchCooperativeKernel(kk.loop, dim3(nb_loop), dim3(NT), args, smem_loop, s);
-    }
-    if (e == cudaSuccess) {
-        FinParams Q;
-        Q.C = a.C;
-        Q.ld = a.ld;
-        Q.I = I;
-        Q.J = J;
-        Q.Jp = Jp;
-        Q.p = a.p;
-        Q.sc = sc;
-        Q.F0 = F;
-        Q.F1 = F + I;
-        Q.st = ls;
-        Q.G = G;
-        Q.k_hi = k_hi;
-        Q.k_lo = k_lo;
-        Q.eps_ln2 = a.eps * LN2;
-        Q.pi = a.out->pi;
-        Q.pi_ld = a.out->pi_ld > 0 ? a.out->pi_ld : J;
-        Q.f_out = a.out->f;
-        Q.fpart = (double2*)colpart;
-        Q.epart = errpart;
-        void* args[] = {&Q};
-        e = cudaLaunchKernel(kfin, dim3(nb_fin), dim3(NT_F), args, 0, s);
-    }
-    if (e == cudaSuccess) {
-        sk_finalize_cols<<<(J + 15) / 16, 512, 0, s>>>((const double2*)colpart, nb_fin, Jp, J, a.q, sc, ls, G,
-                                                       a.eps * LN2, a.out->g, a.out->rrh_load, colerr);
-        sk_summary<<<1, 256, 0, s>>>(errpart, nb_fin, colerr, J, sc, ls, summ);
-        e = cudaMemcpyAsync(sum_host, summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, s);
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    B.sc = (DevScalars*)state;
+    B.ls = (LoopState*)(state + 256);
+    B.summ = (SolveSummary*)(state + 512);
+    B.cols = (double2*)(base + NA_COLS);
+    B.G = (double*)(base + NA_G);
+    B.errpart = (double*)(base + NA_ERRPART);
+    B.colpart = (void*)(base + NA_COLPART);
+    B.F = (float2*)(base + NA_F);
+    // The state words are cleared at the start of every call (the array keeps the last
+    // call's data); enqueue_solve does that first.
+    cudaError_t e = enqueue_solve(a, kk, LL, nb_fin, smem_fin, B, 1LL << 24, a.stream, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sum_host, B.summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, a.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(a.stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return OT_ECUDA;

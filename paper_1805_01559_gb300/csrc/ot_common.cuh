@@ -165,4 +165,154 @@ __device__ __forceinline__ void load_row(const float* __restrict__ row, int J, i
     }
 }
 
+
+// ---- mbarrier + bulk-copy (TMA) helpers, CTA scope ---------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Make barrier initialisation visible to the async (bulk-copy) proxy.
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// As mbar_try_wait, but a thread whose phase is not complete is suspended in hardware for
+// up to `ns` nanoseconds (woken as soon as the phase completes) instead of returning at
+// once, so waiting warps do not take issue slots from working ones.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `bar` with the given parity, at most `limit` polls.  On expiry the
+// device status becomes DEV_ETIMEOUT; a status already set by another CTA also ends the wait.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit, int* status) {
+    long long n = 0;
+    while (!mbar_try_wait_sleep(bar, parity, 1000)) {
+        if ((++n & 1023) == 0 && ld_volatile_i32(status) != DEV_OK) return false;
+        if (n > limit) {
+            atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// One bulk copy global -> shared completing on `bar` (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Grid barrier for kernels whose CTAs hold a warp that does not take part (a copy producer):
+// the CTA-level synchronisation is the named barrier `bar_id` over `nthreads` threads.  One
+// thread publishes the CTA's arrival with a release add (ordered after the CTA's writes by
+// the named barrier) and polls with acquire loads; the second named barrier passes what it
+// acquired on to the rest of the CTA.  Polls sleep only after the first few hundred.
+__device__ __forceinline__ bool grid_barrier_named(unsigned* count, unsigned target, int* status,
+                                                   long long spin_limit, int bar_id, int nthreads,
+                                                   int* s_ok) {
+    bar_named(bar_id, nthreads);
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        long long n = 0;
+        while (ld_acquire_u32(count) < target) {
+            ++n;
+            if ((n & 63) == 0 && ld_volatile_i32(status) != DEV_OK) { ok = 0; break; }
+            if (n > spin_limit) {
+                atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
+                ok = 0;
+                break;
+            }
+            if (n > 256) __nanosleep(32);
+        }
+        *s_ok = ok;
+    }
+    bar_named(bar_id, nthreads);
+    return *(volatile int*)s_ok != 0;
+}
+
+// ---- FP32 pair ("double-float") arithmetic: GB300 issues FP64 at a small fraction of the
+// FP32 rate, so sums that need more than 24 bits are carried as unevaluated pairs. -------
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) + b, renormalised.
+__device__ __forceinline__ float2 df_add(float2 a, float b) {
+    float s, e;
+    two_sum_f(a.x, b, s, e);
+    e += a.y;
+    float h, l;
+    two_sum_f(s, e, h, l);
+    return make_float2(h, l);
+}
+
+__device__ __forceinline__ float2 df_add2(float2 a, float2 b) {
+    float s, e;
+    two_sum_f(a.x, b.x, s, e);
+    e += a.y + b.y;
+    float h, l;
+    two_sum_f(s, e, h, l);
+    return make_float2(h, l);
+}
+
+__device__ __forceinline__ float2 warp_sum_df(float2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float2 w;
+        w.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+        w.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+        v = df_add2(v, w);
+    }
+    return v;
+}
+
+// log2 of a positive pair value: exact exponent plus the FP32 log2 of the mantissa, so the
+// absolute error is that of log2f on [1, 2) (a few 2^-24), whatever the magnitude.
+__device__ __forceinline__ float2 df_log2(float2 a) {
+    int e;
+    const float m = frexpf(a.x, &e);  // a.x = m 2^e, m in [0.5, 1)
+    const float lm = log2f(m) + a.y / (a.x * 0.69314718f);
+    return make_float2((float)e, lm);  // value = e + lm (both exact in the pair)
+}
+
 }  // namespace ota
