@@ -323,6 +323,30 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_solve(args):
+    """Driver for ncu captures of the solver: build the 50,000 x 800 instance, then
+    `--profile-solves` solves at eps = 0.1 median(C) (capture the last with -s/-c)."""
+    import torch
+
+    from paper_1805_01559_gb300 import binding
+    inst = make_inputs()
+    dev = torch.device("cuda", 0)
+    G = torch.from_numpy(np.ascontiguousarray(inst.G, dtype=np.float32)).to(dev)
+    P = torch.from_numpy(inst.P.astype(np.float32)).to(dev)
+    lam = torch.from_numpy(inst.lam.astype(np.float32)).to(dev)
+    q = torch.from_numpy(inst.q.astype(np.float32)).to(dev)
+    ctx = binding.Context(0)
+    R = ctx.build_rates(G, P, inst.N0, inst.W_hz)
+    C, med = ctx.build_cost(R, inst.mu, eps_rel=1.0)
+    for _ in range(args.profile_solves):
+        res = ctx.solve_cost(C, lam, q, 0.1 * med, tol=TOL, max_iter=MAX_ITER)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": "c2_50000x800 eps=0.1*median", "iters": res.iters,
+                      "cost": res.transport_cost}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,7 +355,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=12_500)
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="only run this many solves of the benchmark instance (for profiler captures)")
     args = ap.parse_args()
+    if args.profile_solves > 0:
+        return run_profile_solve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
