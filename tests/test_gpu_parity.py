@@ -102,6 +102,32 @@ def test_median_bit_exact(ctx, n):
     assert ctx.median_f32(_t(x)) == oracle.median(x.astype(np.float64))
 
 
+@pytest.mark.parametrize("kind", ["sample_misses", "heavy_ties", "even_large"])
+def test_median_bracket_fallback(ctx, kind):
+    """Above 2^20 entries the median brackets the middle ranks with a strided sample.  A
+    sample that misses the middle (every 20th entry tiny) or a bracket holding far too many
+    ties must fall back to the full select and stay exact."""
+    n = 65536 * 20
+    rng = _rng(n + len(kind))
+    x = rng.lognormal(0.0, 2.0, n).astype(np.float32)
+    if kind == "sample_misses":
+        x[::20] = 0.0
+    elif kind == "heavy_ties":
+        x[: (3 * n) // 4] = np.float32(1.5)
+    else:
+        x = x[: n - 2]
+    assert ctx.median_f32(_t(x)) == oracle.median(x.astype(np.float64))
+
+
+def test_cost_median_strided_large(ctx):
+    """Cost median over a padded (ld > J) matrix large enough for the sampled bracket."""
+    rng = _rng(7)
+    I, J = 2000, 801
+    R32 = rng.lognormal(np.log(2e7), 1.5, (I, J)).astype(np.float32)
+    C, eps = ctx.build_cost(_t(R32), 1e-6, eps_rel=1.0)
+    assert eps == oracle.median(_np(C).astype(np.float64))
+
+
 def test_maxsinr_matches_oracle(ctx):
     inst = ins.config1()
     R32 = oracle.rates(inst.G.astype(np.float32), inst.P, inst.N0, inst.W_hz).astype(np.float32)
