@@ -262,6 +262,88 @@ ot_status ot_assoc_solve_lowp(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, c
                               int32_t max_iter, int32_t warm_start, int32_t format,
                               double absorb_log2, ot_assoc_result* out, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched ragged solves: many independent instances of Algorithm 1 (each its own I x J
+ * cost, marginals and eps) in ONE persistent launch.  The CTAs of the launch form groups;
+ * each group takes instances from a queue (largest first), solves one exactly as
+ * ot_assoc_solve_cost does (same arithmetic, same stopping rule) and finalizes it in the
+ * same launch.  The group size and the stage size (rows of C per bulk copy) come from
+ * the context's tuning table per size bucket (ot_assoc_autotune), else from defaults.
+ * Limits: J <= 1024 per instance (OT_EUNSUPPORTED above); C read in place, so it must be
+ * 16-byte aligned with ld % 4 == 0 (OT_EINVAL otherwise).
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    const float* C;     /* [device] I x J cost, ld (0 = J), 16-byte aligned rows */
+    int64_t ld;
+    int64_t I;
+    int32_t J;
+    int32_t warm_start; /* != 0: start from b = exp(g / eps) with the g given below */
+    const float* p;     /* [device] I, > 0 */
+    const float* q;     /* [device] J, > 0, sum q = sum p (1e-5 relative) */
+    double eps;         /* > 0, absolute */
+    double tol;         /* >= 0, row residual of the unit-mass plan */
+    int32_t max_iter;   /* >= 1 */
+    int32_t reserved;
+    double* f;          /* [device] I: potentials f_i (required) */
+    double* g;          /* [device] J: potentials g_j (required; read first when warm_start) */
+    double* rrh_load;   /* [device] J: rho_j = sum_i C_ij pi_ij, or NULL */
+    float* pi;          /* [device] I x J plan, or NULL */
+    int64_t pi_ld;      /* 0 = J */
+} ot_assoc_instance;
+
+typedef struct {
+    double transport_cost; /* sum_ij C_ij pi_ij (caller's mass units), FP64 reduction */
+    double marg_err_row;   /* sum_i |sum_j pi_ij - p_i| / sum p */
+    double marg_err_col;   /* sum_j |sum_i pi_ij - q_j| / sum p */
+    double err_loop;       /* residual estimate that stopped the loop */
+    int32_t iters;         /* completed iterations */
+    int32_t status;        /* OT_OK, OT_NOT_CONVERGED, OT_EINVAL (bad marginals or a
+                              numerical breakdown), OT_ETIMEOUT (the launch gave up) */
+    int32_t converged;     /* 1 when the loop stopped at residual <= tol */
+    int32_t reserved;
+} ot_assoc_instance_result;
+
+/* A planned batch: schedule, device tables and (unless OT_BATCH_NO_GRAPH) a captured CUDA
+ * graph holding descriptor upload, control reset, the persistent launch and the result
+ * download.  Owned by the caller; destroy with ot_assoc_batch_destroy before the context. */
+typedef struct ot_assoc_batch ot_assoc_batch;
+
+enum { OT_BATCH_NO_GRAPH = 1 /* enqueue the launch directly instead of replaying a graph */ };
+
+/* One-shot: plan, run on `stream`, wait, fill res[0..n) [host].  Returns OT_OK when the
+ * launch completed (per-instance outcomes are in res[k].status), else an error. */
+ot_status ot_assoc_solve_batched(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int32_t n,
+                                 ot_assoc_instance_result* res, void* stream);
+
+/* Plan a batch of n instances [host array, copied] and capture its graph. */
+ot_status ot_assoc_batch_create(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int32_t n,
+                                int32_t flags, ot_assoc_batch** out);
+
+/* Replace instance k's pointers and parameters (I, J and ld must stay the same); takes
+ * effect at the next launch.  Must not be called while a launch of this batch is running. */
+ot_status ot_assoc_batch_set(ot_assoc_batch* b, int32_t k, const ot_assoc_instance* inst);
+
+/* Enqueue one run of the batch on `stream` (graph replay); returns at once. */
+ot_status ot_assoc_batch_launch(ot_assoc_batch* b, void* stream);
+
+/* Synchronise `stream` and fill res[0..n) [host] (res may be NULL). */
+ot_status ot_assoc_batch_wait(ot_assoc_batch* b, void* stream, ot_assoc_instance_result* res);
+
+void ot_assoc_batch_destroy(ot_assoc_batch* b);
+
+/* Measure, for every size bucket present in inst[0..n), the candidate (group size, stage
+ * size) pairs on those instances (iters iterations each, outputs to scratch, the callers'
+ * buffers untouched) and store the fastest per bucket in the context's tuning table. */
+ot_status ot_assoc_autotune(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int32_t n,
+                            int32_t iters, void* stream);
+
+/* Tuning table access: bucket b in [0, 15) (cells class * 3 + J class); gsize 0 = untuned. */
+ot_status ot_assoc_tuning_get(const ot_assoc_ctx* ctx, int32_t bucket, int32_t* gsize,
+                              int32_t* stage_bytes, double* rate);
+ot_status ot_assoc_tuning_set(ot_assoc_ctx* ctx, int32_t bucket, int32_t gsize, int32_t stage_bytes);
+/* Size bucket of an I x J instance. */
+int32_t ot_assoc_bucket(int64_t I, int32_t J);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,42 @@ class ot_assoc_timings(ctypes.Structure):
     ]
 
 
+class ot_assoc_instance(ctypes.Structure):
+    _fields_ = [
+        ("C", ctypes.c_void_p),
+        ("ld", ctypes.c_int64),
+        ("I", ctypes.c_int64),
+        ("J", ctypes.c_int32),
+        ("warm_start", ctypes.c_int32),
+        ("p", ctypes.c_void_p),
+        ("q", ctypes.c_void_p),
+        ("eps", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("f", ctypes.c_void_p),
+        ("g", ctypes.c_void_p),
+        ("rrh_load", ctypes.c_void_p),
+        ("pi", ctypes.c_void_p),
+        ("pi_ld", ctypes.c_int64),
+    ]
+
+
+class ot_assoc_instance_result(ctypes.Structure):
+    _fields_ = [
+        ("transport_cost", ctypes.c_double),
+        ("marg_err_row", ctypes.c_double),
+        ("marg_err_col", ctypes.c_double),
+        ("err_loop", ctypes.c_double),
+        ("iters", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+OT_BATCH_NO_GRAPH = 1
+
 # (name, restype, argtypes) of every exported entry point in include/ot_assoc.h
 _VP, _I64, _I32, _D, _SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
 _PD = ctypes.POINTER(ctypes.c_double)
@@ -97,6 +133,18 @@ SIGNATURES = {
                                           ctypes.POINTER(ot_assoc_result), _VP]),
     "ot_assoc_solve_lowp": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,
                                            _I32, _D, ctypes.POINTER(ot_assoc_result), _VP]),
+    "ot_assoc_solve_batched": (ctypes.c_int, [_VP, ctypes.POINTER(ot_assoc_instance), _I32,
+                                              ctypes.POINTER(ot_assoc_instance_result), _VP]),
+    "ot_assoc_batch_create": (ctypes.c_int, [_VP, ctypes.POINTER(ot_assoc_instance), _I32, _I32,
+                                             ctypes.POINTER(_VP)]),
+    "ot_assoc_batch_set": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ot_assoc_instance)]),
+    "ot_assoc_batch_launch": (ctypes.c_int, [_VP, _VP]),
+    "ot_assoc_batch_wait": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ot_assoc_instance_result)]),
+    "ot_assoc_batch_destroy": (None, [_VP]),
+    "ot_assoc_autotune": (ctypes.c_int, [_VP, ctypes.POINTER(ot_assoc_instance), _I32, _I32, _VP]),
+    "ot_assoc_tuning_get": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _PD]),
+    "ot_assoc_tuning_set": (ctypes.c_int, [_VP, _I32, _I32, _I32]),
+    "ot_assoc_bucket": (_I32, [_I64, _I32]),
 }
 
 
@@ -344,3 +392,156 @@ class Context:
                                          float(absorb_log2), ctypes.byref(r), _stream(stream))
         self._check(st, allow_nc=True)
         return self._pack(r, f, g, pi, load)
+
+
+# ---- batched ragged solves ------------------------------------------------------------------
+@dataclasses.dataclass
+class Instance:
+    """One instance of a batch: cost C (I x J, float32, 16-byte aligned rows), marginals, eps.
+    f, g (float64) receive the potentials; g is read first when warm_start."""
+    C: torch.Tensor
+    p: torch.Tensor
+    q: torch.Tensor
+    eps: float
+    tol: float = 1e-6
+    max_iter: int = 2000
+    warm_start: bool = False
+    f: Optional[torch.Tensor] = None
+    g: Optional[torch.Tensor] = None
+    rrh_load: Optional[torch.Tensor] = None
+    pi: Optional[torch.Tensor] = None
+
+    def prepare(self, want_load: bool = True) -> "Instance":
+        _need(self.C, torch.float32, "C", 2)
+        _need(self.p, torch.float32, "p", 1)
+        _need(self.q, torch.float32, "q", 1)
+        I, J = self.C.shape
+        dev = self.C.device
+        if self.f is None:
+            self.f = torch.empty(I, dtype=torch.float64, device=dev)
+        if self.g is None:
+            self.g = torch.zeros(J, dtype=torch.float64, device=dev)
+        if want_load and self.rrh_load is None:
+            self.rrh_load = torch.empty(J, dtype=torch.float64, device=dev)
+        return self
+
+    def to_c(self) -> ot_assoc_instance:
+        I, J = self.C.shape
+        d = ot_assoc_instance()
+        d.C = self.C.data_ptr()
+        d.ld = self.C.stride(0)
+        d.I = I
+        d.J = J
+        d.warm_start = 1 if self.warm_start else 0
+        d.p = self.p.data_ptr()
+        d.q = self.q.data_ptr()
+        d.eps = float(self.eps)
+        d.tol = float(self.tol)
+        d.max_iter = int(self.max_iter)
+        d.f = self.f.data_ptr()
+        d.g = self.g.data_ptr()
+        d.rrh_load = self.rrh_load.data_ptr() if self.rrh_load is not None else None
+        d.pi = self.pi.data_ptr() if self.pi is not None else None
+        d.pi_ld = self.pi.stride(0) if self.pi is not None else 0
+        return d
+
+
+@dataclasses.dataclass
+class InstanceResult:
+    transport_cost: float
+    marg_err_row: float
+    marg_err_col: float
+    err_loop: float
+    iters: int
+    status: int
+    converged: bool
+
+
+def _results(arr, n) -> list:
+    return [InstanceResult(arr[k].transport_cost, arr[k].marg_err_row, arr[k].marg_err_col, arr[k].err_loop,
+                           arr[k].iters, arr[k].status, bool(arr[k].converged)) for k in range(n)]
+
+
+class Batch:
+    """A planned batch (ot_assoc_batch): schedule, device tables and a captured CUDA graph."""
+
+    def __init__(self, ctx: "Context", instances, graph: bool = True):
+        self._ctx = ctx
+        self._L = ctx._L
+        self.instances = [x.prepare() for x in instances]
+        n = len(self.instances)
+        arr = (ot_assoc_instance * n)(*[x.to_c() for x in self.instances])
+        h = ctypes.c_void_p()
+        st = self._L.ot_assoc_batch_create(ctx.handle, arr, n, 0 if graph else OT_BATCH_NO_GRAPH, ctypes.byref(h))
+        ctx._check(st)
+        self._h = h
+        self._res = (ot_assoc_instance_result * n)()
+
+    def set(self, k: int, inst: Instance) -> None:
+        inst.prepare()
+        d = inst.to_c()
+        self._ctx._check(self._L.ot_assoc_batch_set(self._h, int(k), ctypes.byref(d)))
+        self.instances[k] = inst
+
+    def launch(self, stream=None) -> None:
+        self._ctx._check(self._L.ot_assoc_batch_launch(self._h, _stream(stream)))
+
+    def wait(self, stream=None) -> list:
+        self._ctx._check(self._L.ot_assoc_batch_wait(self._h, _stream(stream), self._res))
+        return _results(self._res, len(self.instances))
+
+    def run(self, stream=None) -> list:
+        self.launch(stream)
+        return self.wait(stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ot_assoc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ctx_solve_batched(self, instances, stream=None) -> list:
+    """One-shot batched solve (ot_assoc_solve_batched); fills each instance's f, g, rrh_load."""
+    inst = [x.prepare() for x in instances]
+    n = len(inst)
+    arr = (ot_assoc_instance * n)(*[x.to_c() for x in inst])
+    res = (ot_assoc_instance_result * n)()
+    self._check(self._L.ot_assoc_solve_batched(self._h, arr, n, res, _stream(stream)))
+    return _results(res, n)
+
+
+def _ctx_autotune(self, instances, iters: int = 8, stream=None) -> None:
+    inst = [x.prepare() for x in instances]
+    n = len(inst)
+    arr = (ot_assoc_instance * n)(*[x.to_c() for x in inst])
+    self._check(self._L.ot_assoc_autotune(self._h, arr, n, int(iters), _stream(stream)))
+
+
+def _ctx_tuning(self) -> list:
+    out = []
+    for b in range(15):
+        gs, stg, rate = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+        self._check(self._L.ot_assoc_tuning_get(self._h, b, ctypes.byref(gs), ctypes.byref(stg), ctypes.byref(rate)))
+        out.append({"bucket": b, "gsize": gs.value, "stage": stg.value, "rate": rate.value})
+    return out
+
+
+def _ctx_set_tuning(self, bucket: int, gsize: int, stage: int) -> None:
+    self._check(self._L.ot_assoc_tuning_set(self._h, int(bucket), int(gsize), int(stage)))
+
+
+def bucket(I: int, J: int) -> int:
+    return int(lib().ot_assoc_bucket(int(I), int(J)))
+
+
+Context.solve_batched = _ctx_solve_batched
+Context.autotune = _ctx_autotune
+Context.tuning = _ctx_tuning
+Context.set_tuning = _ctx_set_tuning
+Context.batch = lambda self, instances, graph=True: Batch(self, instances, graph)

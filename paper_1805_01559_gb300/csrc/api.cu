@@ -165,16 +165,7 @@ static ot_status finish(ot_assoc_ctx* ctx, const SolveSummary& s, ot_assoc_resul
     return st;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
+using DeviceGuard = DeviceGuardLite;
 
 }  // namespace ota
 
@@ -480,5 +471,75 @@ ot_status ot_assoc_solve_lowp(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, c
     if (st) return st;
     return finish(ctx, sum, out);
 }
+
+ot_status ot_assoc_batch_create(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int32_t n, int32_t flags,
+                                ot_assoc_batch** out) {
+    if (!ctx) return OT_EINVAL;
+    if (!out) return set_error(ctx, OT_EINVAL, "null output pointer");
+    DeviceGuard g(ctx->device);
+    return batch_create(ctx, inst, n, flags, out);
+}
+
+ot_status ot_assoc_batch_set(ot_assoc_batch* b, int32_t k, const ot_assoc_instance* inst) {
+    if (!b) return OT_EINVAL;
+    return batch_set(b, k, inst);
+}
+
+ot_status ot_assoc_batch_launch(ot_assoc_batch* b, void* stream) {
+    if (!b) return OT_EINVAL;
+    return batch_launch(b, (cudaStream_t)stream);
+}
+
+ot_status ot_assoc_batch_wait(ot_assoc_batch* b, void* stream, ot_assoc_instance_result* res) {
+    if (!b) return OT_EINVAL;
+    return batch_wait(b, (cudaStream_t)stream, res);
+}
+
+void ot_assoc_batch_destroy(ot_assoc_batch* b) { batch_destroy(b); }
+
+ot_status ot_assoc_solve_batched(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int32_t n,
+                                 ot_assoc_instance_result* res, void* stream) {
+    if (!ctx) return OT_EINVAL;
+    if (!res) return set_error(ctx, OT_EINVAL, "null result array");
+    DeviceGuard g(ctx->device);
+    ot_assoc_batch* b = nullptr;
+    ot_status st = batch_create(ctx, inst, n, OT_BATCH_NO_GRAPH, &b);
+    if (st) return st;
+    st = batch_launch(b, (cudaStream_t)stream);
+    if (!st) st = batch_wait(b, (cudaStream_t)stream, res);
+    batch_destroy(b);
+    return st;
+}
+
+ot_status ot_assoc_autotune(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int32_t n, int32_t iters,
+                            void* stream) {
+    if (!ctx) return OT_EINVAL;
+    if (!inst || n <= 0) return set_error(ctx, OT_EINVAL, "empty tuning set");
+    DeviceGuard g(ctx->device);
+    return batch_autotune(ctx, inst, n, iters, (cudaStream_t)stream);
+}
+
+ot_status ot_assoc_tuning_get(const ot_assoc_ctx* ctx, int32_t bucket, int32_t* gsize, int32_t* stage_bytes,
+                              double* rate) {
+    if (!ctx || bucket < 0 || bucket >= TUNE_BUCKETS) return OT_EINVAL;
+    if (gsize) *gsize = ctx->tune[bucket].gsize;
+    if (stage_bytes) *stage_bytes = ctx->tune[bucket].stage;
+    if (rate) *rate = ctx->tune[bucket].rate;
+    return OT_OK;
+}
+
+ot_status ot_assoc_tuning_set(ot_assoc_ctx* ctx, int32_t bucket, int32_t gsize, int32_t stage_bytes) {
+    if (!ctx) return OT_EINVAL;
+    if (bucket < 0 || bucket >= TUNE_BUCKETS) return set_error(ctx, OT_EINVAL, "bucket out of range");
+    if (gsize < 0 || (gsize > 0 && ctx->num_sms % gsize != 0))
+        return set_error(ctx, OT_EINVAL, "group size must divide the SM count (%d)", ctx->num_sms);
+    if (stage_bytes < 0) return set_error(ctx, OT_EINVAL, "stage size must be >= 0");
+    ctx->tune[bucket].gsize = gsize;
+    ctx->tune[bucket].stage = stage_bytes;
+    ctx->tune[bucket].rate = 0.0;
+    return OT_OK;
+}
+
+int32_t ot_assoc_bucket(int64_t I, int32_t J) { return batch_bucket(I, J); }
 
 }  // extern "C"

@@ -26,7 +26,16 @@ enum ScratchSlot {
     SLOT_KT,           // stored kernel (low precision form)
     SLOT_SCAL,         // scaling vectors u, v, drift references (low precision form)
     SLOT_ALIGN,        // 16-byte-aligned copies of unaligned caller inputs (G, R)
+    SLOT_TUNE,         // autotuner outputs (potentials of the timed runs)
     SLOT_COUNT
+};
+
+// Batched solver tuning: one entry per size bucket (cells class x J class).
+static constexpr int TUNE_BUCKETS = 15;
+struct TuneEntry {
+    int gsize = 0;   // CTAs per instance group (0 = not tuned: use the default)
+    int stage = 0;   // bytes of C per bulk copy (target)
+    double rate = 0; // measured cells * iterations / s of the chosen pair
 };
 
 struct ScratchBuf {
@@ -50,6 +59,7 @@ struct ot_assoc_ctx {
     bool timing = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     ot_assoc_timings last_timings = {};
+    ota::TuneEntry tune[ota::TUNE_BUCKETS];
 };
 
 namespace ota {
@@ -127,6 +137,28 @@ ot_status launch_cost(ot_assoc_ctx* ctx, const float* R, int64_t ld_r, int64_t I
 // the result (double) to *out_dev.  Requires no NaN.
 ot_status launch_median(ot_assoc_ctx* ctx, const float* x, int64_t rows, int64_t cols, int64_t ld,
                         double* out_dev, cudaStream_t s);
+// Batched ragged solve (k_batch.cu).
+int batch_bucket(int64_t I, int J);
+ot_status batch_create(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int n, int flags, ot_assoc_batch** out,
+                       int forced_gsize = 0, int forced_stage = 0);
+ot_status batch_set(ot_assoc_batch* b, int k, const ot_assoc_instance* a);
+ot_status batch_launch(ot_assoc_batch* b, cudaStream_t s);
+ot_status batch_wait(ot_assoc_batch* b, cudaStream_t s, ot_assoc_instance_result* res);
+void batch_destroy(ot_assoc_batch* b);
+ot_status batch_autotune(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int n, int iters, cudaStream_t s);
+
+// Make `dev` current for the lifetime of the guard (restores the previous device).
+struct DeviceGuardLite {
+    int prev = -1;
+    explicit DeviceGuardLite(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuardLite() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 ot_status launch_maxsinr(ot_assoc_ctx* ctx, const float* R, int64_t ld_r, const float* lam,
                          int64_t I, int J, double mu, int32_t* assoc, double* Lambda,
                          double* total_dev, cudaStream_t s);

@@ -1,0 +1,720 @@
+// Sinkhorn solver core shared by the single-instance and the batched persistent kernels
+// (Algorithm 1 of the paper, Sec. III-B, in the log2-unit form described in k_sinkhorn.cu):
+// constants, FP32-pair helpers, the row-streaming producer and the consumer warps' loop.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "ot_common.cuh"
+
+namespace ota {
+
+static constexpr int NT_F = 256;  // threads per CTA of the finalize kernel (row blocks)
+static constexpr double LN2 = 0.69314718055994530942;
+static constexpr double LOG2E = 1.44269504088896340736;
+
+enum : int { DEV_ENUMERIC = -7 };
+
+struct DevScalars {
+    double sp, sq;  // sums of the caller's p and q
+    double inv_sp, inv_sq;
+    float inv_sp_f;
+    int status;
+};
+
+struct LoopState {
+    unsigned bar;
+    int status;
+    int iters;
+    int converged;
+    double err;
+};
+
+template <int TW, int VPT>
+__device__ __forceinline__ void load_G(const double* __restrict__ G, int J, int tl, float4 (&g)[VPT]) {
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int col = 4 * (tl + 32 * TW * v);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) comp(g[v], c) = (col + c < J) ? (float)G[col + c] : 0.0f;
+    }
+}
+
+// Cell exponent x = F + G - k C in log2 units, with F = F_hi + F_lo (FP32 pair) and
+// k = k_hi + k_lo.  The exact FMA product cancels the large parts F_hi - C k_hi first, so
+// the only roundings happen at the magnitude of |G| and |x|, however large k C and F are on
+// the support.  k_lo > 0 always (see split_k): a +inf cost (masked column, forbidden link)
+// gives -inf and never inf - inf.
+__device__ __forceinline__ float expo(float F_hi, float F_lo_plus_G, float c, float k_hi, float k_lo) {
+    return fmaf(-c, k_hi, F_hi) + fmaf(-c, k_lo, F_lo_plus_G);
+}
+
+// Error-free sum a + b = s + e (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) - d as a renormalised FP32 pair.
+__device__ __forceinline__ float2 df_sub(float2 f, float d) {
+    float s, e;
+    two_sum(f.x, -d, s, e);
+    e += f.y;
+    float h, l;
+    two_sum(s, e, h, l);
+    return make_float2(h, l);
+}
+
+// k = k_hi + k_lo with k_hi rounded down and 0 < k_lo <= ulp(k_hi): the low part is never
+// zero or negative, so -inf * k_lo = -inf and no inf - inf can occur for C = +inf.
+static inline void split_k(double k, float* hi, float* lo) {
+    float h = (float)k;
+    if ((double)h >= k) h = nextafterf(h, 0.0f);
+    float l = (float)(k - (double)h);
+    if (!(l > 0.0f)) l = 1.4e-45f;  // smallest subnormal; adds nothing measurable
+    *hi = h;
+    *lo = l;
+}
+
+// ------------------------------------------------------------------------------------------
+// Row streaming: one producer warp copies contiguous blocks of rows of C into a ring of
+// shared-memory stages with bulk copies; the consumer warps work on them.
+// ------------------------------------------------------------------------------------------
+// Consumer warps per CTA: 12 (3 per SM sub-partition, so 13 warps keep 128 registers each)
+// when a team is 1, 2 or 4 warps; 8 when a row needs a team of 8 warps.
+template <int TW>
+struct Cons {
+    static constexpr int NCW = (TW == 8) ? 8 : 12;
+    static constexpr int NT = 32 * (NCW + 1);  // + one producer warp
+};
+static constexpr int MAX_STAGES = 8;
+static constexpr int CONS_BAR = 15;          // named barrier of the consumer warps
+static constexpr int SMEM_HDR = 256;         // mbarriers at the start of dynamic smem
+
+struct StreamCfg {
+    int rows_per_stage;  // NTEAMS * rpt
+    int rpt;             // rows per team per stage
+    int stages;
+    int stage_floats;    // rows_per_stage * ld
+    int rmax;            // most rows any CTA owns
+    int off_G;           // byte offsets inside dynamic smem
+    int off_F;
+    int off_P;
+    int off_ring;
+};
+
+// Column potentials as FP32 in shared memory (padding columns 0).
+__device__ __forceinline__ void load_G_smem(const double* __restrict__ G, int J, int Jp, float* Gs, int tid,
+                                            int nthreads) {
+    for (int j = tid; j < Jp; j += nthreads) Gs[j] = (j < J) ? (float)G[j] : 0.0f;
+}
+
+// log2(r) for the row and column corrections: a short series when r is within 2^-7 of 1
+// (|u|^5/5 < 2^-37 relative to the result), the SFU logarithm otherwise.
+__device__ __forceinline__ float log2_corr(float r) {
+    const float u = r - 1.0f;  // exact for r in [0.5, 2]
+    const float series = u * (1.0f + u * (-0.5f + u * (0.33333334f + u * -0.25f))) * 1.44269504f;
+    const float sfu = __log2f(r);
+    return fabsf(u) < 0.0078125f ? series : sfu;
+}
+
+// A lane's chunk v is certainly inside the row when the dispatch chose VPT = ceil(J4 / 32)
+// for a one-warp team (pick_kernels does exactly that for TW = 1): then every chunk but the
+// lane's last ends at or before column J.  Wider teams check every chunk.
+template <int TW, int VPT>
+__device__ __forceinline__ constexpr bool chunk_inside(int v) {
+    return TW == 1 && v < VPT - 1;
+}
+
+// Row load from a shared-memory stage; chunks that can leave the row are checked.
+template <int TW, int VPT>
+__device__ __forceinline__ void load_row_smem(const float* row, int J, int tl, float4 (&x)[VPT]) {
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int col = 4 * (tl + 32 * TW * v);
+        if (chunk_inside<TW, VPT>(v)) {
+            x[v] = *reinterpret_cast<const float4*>(row + col);
+        } else if (col < J) {
+            float4 t = *reinterpret_cast<const float4*>(row + col);
+            if (col + 4 > J) {
+                if (col + 1 >= J) t.y = INFINITY;
+                if (col + 2 >= J) t.z = INFINITY;
+                if (col + 3 >= J) t.w = INFINITY;
+            }
+            x[v] = t;
+        } else {
+            x[v] = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+        }
+    }
+}
+
+// Producer: stream the CTA's row blocks sweep after sweep until the consumers raise s_stop,
+// then wait for every copy still in flight before leaving.
+__device__ __forceinline__ void stream_rows_producer(const float* C, int64_t ld, int64_t r0, int64_t r1,
+                                                     const StreamCfg& S, float* ring, uint64_t* full,
+                                                     uint64_t* empty, volatile int* s_stop, int* status,
+                                                     long long spin) {
+    const int nblk = (int)((r1 - r0 + S.rows_per_stage - 1) / S.rows_per_stage);
+    uint32_t seq = 0;
+    bool stop = (nblk <= 0);
+    while (!stop) {
+        for (int k = 0; k < nblk && !stop; ++k) {
+            const int st = (int)(seq % (uint32_t)S.stages);
+            const uint32_t use = seq / (uint32_t)S.stages;
+            if (use > 0) {  // wait for the consumers to release this stage's previous copy
+                long long n = 0;
+                while (!mbar_try_wait_sleep(&empty[st], (use - 1) & 1u, 500)) {
+                    if (*s_stop) { stop = true; break; }
+                    if ((++n & 1023) == 0 && ld_volatile_i32(status) != DEV_OK) { stop = true; break; }
+                    if (n > spin) {
+                        atomicCAS(status, DEV_OK, DEV_ETIMEOUT);
+                        stop = true;
+                        break;
+                    }
+                }
+                if (stop) break;
+            }
+            if (*s_stop) { stop = true; break; }
+            const int64_t row0 = r0 + (int64_t)k * S.rows_per_stage;
+            const int rows = (int)min((int64_t)S.rows_per_stage, r1 - row0);
+            const uint32_t bytes = (uint32_t)(rows * ld * (int64_t)sizeof(float));
+            mbar_arrive_expect_tx(&full[st], bytes);
+            bulk_g2s(ring + (size_t)st * S.stage_floats, C + row0 * ld, bytes, &full[st]);
+            ++seq;
+        }
+    }
+    // Leave no copy in flight: wait for the last use of every stage to land.  This wait has
+    // its own limit (about a second), independent of the caller's spin limit: a copy that was
+    // issued completes on its own, and the CTA must not leave while one can still land.
+    const long long drain_limit = spin > (1LL << 20) ? spin : (1LL << 20);
+    for (int st = 0; st < S.stages; ++st) {
+        if (seq <= (uint32_t)st) continue;
+        const uint32_t uses = (seq - (uint32_t)st + S.stages - 1) / (uint32_t)S.stages;
+        long long n = 0;
+        while (!mbar_try_wait_sleep(&full[st], (uses - 1) & 1u, 1000) && ++n <= drain_limit) {
+        }
+    }
+}
+
+struct SolveParams {
+    const float* C;
+    int64_t ld;
+    int64_t I;
+    int J;
+    int Jp;
+    const float* p;
+    const float* q;
+    const double* g_warm;                 // warm-start g (natural units) or nullptr
+    const unsigned long long* input_bad;  // nonzero => invalid rates upstream, or nullptr
+    DevScalars* sc;
+    LoopState* st;
+    double* G;        // [3][Jp]: column potentials G^k (log2 units, FP64) in buffer k & 1,
+                      // then log2 q^_j (set once per solve)
+    float2* F_out;    // [I] row potentials of the returned plan (hi, lo)
+    float* colpart;   // [nb][2 * Jp]
+    double* errpart;  // [nb] during setup (sums of p); reused as float2 [nb] residual pairs
+    double k;
+    float k_hi, k_lo;
+    double tol;
+    int max_iter;
+    long long spin;
+};
+
+// Block-aligned row range of CTA b.
+__device__ __forceinline__ void cta_rows(int64_t I, int rs, int b, int nb, int64_t* r0, int64_t* r1) {
+    const int64_t B = (I + rs - 1) / rs;
+    *r0 = (B * b / nb) * rs;
+    *r1 = min(I, (B * (b + 1) / nb) * (int64_t)rs);
+}
+
+// Sum of (s, e) pairs over a warp with error-free additions.
+__device__ __forceinline__ void warp_sum_pair(float& s, float& e) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+        float t, u;
+        two_sum(s, s2, t, u);
+        s = t;
+        e = e + e2 + u;
+    }
+}
+
+// Shared-memory words of the consumer warps (and the producer's stop flag).
+struct SkShared {
+    float red[32];          // team reductions: 2 * NTEAMS * TW <= 24
+    float errf[12];         // per-team row residuals
+    double sh_sum[12][2];   // per-warp setup sums
+    int s_dec, s_ok, s_bad;
+    volatile int s_stop;    // consumers -> producer: stop streaming
+};
+
+// The CTAs that solve one instance together: nb CTAs, this one is number b.  `bar` counts
+// arrivals at the group's barriers (monotonic; every CTA of the group passes the same
+// barriers, `gen` of them so far).  A nonzero *abort ends every wait; *status is the
+// instance's status word (the same word as *abort for a single-instance launch).
+struct GroupCtx {
+    int nb, b;
+    unsigned* bar;
+    unsigned gen;
+    int* abort;
+    int* status;
+};
+
+// The consumer warps' part of one solve (Algorithm 1 on the CTA's rows [r0, r1)): setup,
+// the exact first sweep, then plan-scale sweeps until the loop test stops.  Returns true
+// when the loop stopped normally (the returned plan's row potentials are then in row
+// potential buffer *ret_par of shared memory, and in P.F_out when given), false when the
+// instance failed or a wait gave up.  Either way s_stop is raised for the producer.
+// Every decision that ends the loop is taken identically by every CTA of the group.
+template <int TW, int VPT>
+__device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamCfg& S, GroupCtx& g, SkShared* sh,
+                                             unsigned char* dyn, int64_t r0, int64_t r1, int* ret_par) {
+    constexpr int NCW = Cons<TW>::NCW;
+    constexpr int TT = 32 * TW, NTEAMS = NCW / TW, NC = NCW * 32;
+    static_assert(2 * NTEAMS * TW <= 32 && NTEAMS <= 12 && NCW <= 12, "SkShared sizes");
+    uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
+    uint64_t* empty = full + MAX_STAGES;
+    float* comb = reinterpret_cast<float*>(dyn + SMEM_HDR);    // [ceil(NTEAMS / 2)][Jp]
+    float* Gs = reinterpret_cast<float*>(dyn + S.off_G);       // [Jp]
+    float2* Fs = reinterpret_cast<float2*>(dyn + S.off_F);     // [2][rmax]
+    float* Ps = reinterpret_cast<float*>(dyn + S.off_P);       // [rmax]
+    float* ring = reinterpret_cast<float*>(dyn + S.off_ring);  // [stages][stage_floats]
+    float* red = sh->red;
+    float* errf = sh->errf;
+    double(*sh_sum)[2] = sh->sh_sum;
+    int& s_dec = sh->s_dec;
+    int& s_bad = sh->s_bad;
+    volatile int& s_stop = sh->s_stop;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = g.nb, b = g.b;
+    const int nrow = (int)max((int64_t)0, r1 - r0);
+    int* status = g.status;
+    const int J = P.J, Jp = P.Jp;
+    const int tid = threadIdx.x;
+#define OTA_BARRIER()                                                                              \
+    do {                                                                                           \
+        if (!grid_barrier_named(g.bar, (unsigned)nb * ++g.gen, g.abort, P.spin, CONS_BAR, NC, &sh->s_ok)) { \
+            if (tid == 0) s_stop = 1;                                                              \
+            return false;                                                                          \
+        }                                                                                          \
+    } while (0)
+// After a barrier that no status write can overtake (the next write comes after the next
+// barrier): leave when the instance failed.  Only needed when a failed instance does not
+// also end every wait (batched launches keep the abort word apart from instance status).
+#define OTA_BARRIER_CHECK()                                                                        \
+    do {                                                                                           \
+        OTA_BARRIER();                                                                             \
+        if (g.abort != status && ld_volatile_i32(status) != DEV_OK) {                              \
+            if (tid == 0) s_stop = 1;                                                              \
+            return false;                                                                          \
+        }                                                                                          \
+    } while (0)
+
+    // ---- setup: sums of p (per CTA) and q (every CTA), checks, starting G ----------------
+    {
+        double sp = 0.0;
+        int bad = 0;
+        for (int r = tid; r < nrow; r += NC) {
+            const float v = __ldg(P.p + r0 + r);
+            bad |= !(v > 0.0f) || !isfinite(v);
+            sp += (double)v;
+            Ps[r] = v;
+        }
+        const int gw = b * NCW + warp, nw = nb * NCW;
+        for (int j = gw * 32 + lane; j < J; j += nw * 32) {
+            const double g0 = P.g_warm ? P.g_warm[j] * P.k : 0.0;
+            bad |= !isfinite(g0);
+            P.G[j] = g0;
+        }
+        if (b == 0 && tid == 0 && P.input_bad && *P.input_bad) bad = 1;
+        sp = warp_sum(sp);
+        if (lane == 0) sh_sum[warp][0] = sp;
+        if (bad) atomicOr(&s_bad, 1);
+        bar_named(CONS_BAR, NC);
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NCW; ++w) t += sh_sum[w][0];
+            P.errpart[b] = t;
+            if (s_bad) atomicCAS(status, DEV_OK, DEV_EINVAL);
+        }
+    }
+    OTA_BARRIER_CHECK();
+    double sp = 0.0, sq = 0.0;
+    {
+        // every CTA forms the same totals in the same order
+        double a = 0.0, c = 0.0;
+        int badq = 0;
+        for (int bb = tid; bb < nb; bb += NC) a += P.errpart[bb];
+        for (int j = tid; j < J; j += NC) {
+            const float v = __ldg(P.q + j);
+            badq |= !(v > 0.0f) || !isfinite(v);
+            c += (double)v;
+        }
+        a = warp_sum(a);
+        c = warp_sum(c);
+        if (tid == 0) s_bad = 0;
+        bar_named(CONS_BAR, NC);
+        if (lane == 0) {
+            sh_sum[warp][0] = a;
+            sh_sum[warp][1] = c;
+        }
+        if (badq) atomicOr(&s_bad, 1);
+        bar_named(CONS_BAR, NC);
+        for (int w = 0; w < NCW; ++w) {
+            sp += sh_sum[w][0];
+            sq += sh_sum[w][1];
+        }
+        if (s_bad || !(fabs(sp - sq) <= 1e-5 * sp)) {
+            if (b == 0 && tid == 0) atomicCAS(status, DEV_OK, DEV_EINVAL);
+            if (tid == 0) s_stop = 1;
+            return false;  // the same decision in every CTA
+        }
+        if (b == 0 && tid == 0) {
+            P.sc->sp = sp;
+            P.sc->sq = sq;
+            P.sc->inv_sp = 1.0 / sp;
+            P.sc->inv_sq = 1.0 / sq;
+            P.sc->inv_sp_f = (float)(1.0 / sp);
+            P.sc->status = DEV_OK;
+        }
+    }
+    const double inv_sq = 1.0 / sq;
+    double* LQ = P.G + 2 * Jp;  // log2 q^_j, formed once here (read after the next grid barrier)
+    {
+        const int gw = b * NCW + warp, nw = nb * NCW;
+        for (int j = gw * 32 + lane; j < J; j += nw * 32) LQ[j] = log2((double)__ldg(P.q + j) * inv_sq);
+        const float inv_sp_f = (float)(1.0 / sp);
+        for (int r = tid; r < nrow; r += NC) Ps[r] *= inv_sp_f;  // p^_i
+        bar_named(CONS_BAR, NC);
+    }
+    const Team<TW> tm;
+    const int nblk = (nrow + S.rows_per_stage - 1) / S.rows_per_stage;
+    load_G_smem(P.G, J, Jp, Gs, tid, NC);
+    bar_named(CONS_BAR, NC);
+    uint32_t cseq = 0;
+    int par = 0;
+
+    // ---- sweep 1: exact log-domain iteration ------------------------------------------
+    {
+        float4 M[VPT], Sm[VPT];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            M[v] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+            Sm[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float2* F1 = Fs + S.rmax;  // F'^1 lives in buffer 1
+        for (int kb = 0; kb < nblk; ++kb) {
+            const int st = (int)(cseq % (uint32_t)S.stages);
+            const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
+            const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, g.abort);
+            const int lr0 = kb * S.rows_per_stage;
+            const int rows = min(S.rows_per_stage, nrow - lr0);
+            const float* stage = ring + (size_t)st * S.stage_floats;
+            for (int j = 0; ok && j < S.rpt; ++j) {
+                const int rr = tm.team + NTEAMS * j;
+                if (rr >= rows) break;
+                float4 x[VPT];
+                load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
+                // row maximum of y = G0 - k C (approximate values suffice for the shift)
+                float m = -INFINITY;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    float4 gv = col < Jp ? *reinterpret_cast<const float4*>(Gs + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) m = fmaxf(m, fmaf(-comp(x[v], c), P.k_hi, comp(gv, c)));
+                }
+                m = team_reduce<TW, float, true>(m, red, NTEAMS, tm, par);
+                // z = y - m with the large parts cancelled by the exact product
+                float s = 0.f;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    float4 gv = col < Jp ? *reinterpret_cast<const float4*>(Gs + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float z = expo(-m, comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo);
+                        comp(x[v], c) = z;
+                        s += ex2(z);
+                    }
+                }
+                s = team_reduce<TW, float, false>(s, red, NTEAMS, tm, par);
+                const float ls = log2f(s);
+                if (tm.tl == 0) {  // F'^1 = -LSE2_j(y) = -(m + log2 s), exact as an FP32 pair
+                    float hi, lo;
+                    two_sum(m, ls, hi, lo);
+                    F1[lr0 + rr] = make_float2(-hi, -lo);
+                }
+                const float cst = log2f(Ps[lr0 + rr]) - ls;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float u = comp(x[v], c) + cst;  // log2 pi^(1/2)_ij
+                        float& Mc = comp(M[v], c);
+                        float& Sc = comp(Sm[v], c);
+                        if (u > Mc) {
+                            Sc = fmaf(Sc, ex2(Mc - u), 1.0f);
+                            Mc = u;
+                        } else if (u > -INFINITY) {
+                            Sc += ex2(u - Mc);
+                        }
+                    }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+            ++cseq;
+        }
+        // CTA merge of the (max, sum) pairs in two rounds through the float buffer: the column
+        // maxima first (kept in Gs, which is reloaded after the next grid barrier anyway),
+        // then the sums rescaled to them; teams in a fixed order.
+        constexpr int HALF = (NTEAMS + 1) / 2;
+        for (int round = 0; round < 2; ++round) {  // the first half stores, the second half merges
+            if ((tm.team < HALF) == (round == 0)) {
+                const int slot = round == 0 ? tm.team : tm.team - HALF;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    if (col < Jp) {
+                        float4* d = reinterpret_cast<float4*>(comb + slot * Jp + col);
+                        if (round == 0) {
+                            *d = M[v];
+                        } else {
+                            float4 o = *d;
+                            o.x = fmaxf(o.x, M[v].x);
+                            o.y = fmaxf(o.y, M[v].y);
+                            o.z = fmaxf(o.z, M[v].z);
+                            o.w = fmaxf(o.w, M[v].w);
+                            *d = o;
+                        }
+                    }
+                }
+            }
+            bar_named(CONS_BAR, NC);
+        }
+        for (int j = tid; j < Jp; j += NC) {
+            float mm = comb[j];
+            for (int t = 1; t < HALF; ++t) mm = fmaxf(mm, comb[t * Jp + j]);
+            Gs[j] = mm;
+        }
+        bar_named(CONS_BAR, NC);
+        for (int round = 0; round < 2; ++round) {
+            if ((tm.team < HALF) == (round == 0)) {
+                const int slot = round == 0 ? tm.team : tm.team - HALF;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    if (col < Jp) {
+                        float4 sc;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float Mc = comp(M[v], c), mm = Gs[col + c];
+                            comp(sc, c) = Mc > -INFINITY ? comp(Sm[v], c) * ex2(Mc - mm) : 0.f;
+                        }
+                        float4* d = reinterpret_cast<float4*>(comb + slot * Jp + col);
+                        if (round == 0) {
+                            *d = sc;
+                        } else {
+                            float4 o = *d;
+                            o.x += sc.x;
+                            o.y += sc.y;
+                            o.z += sc.z;
+                            o.w += sc.w;
+                            *d = o;
+                        }
+                    }
+                }
+            }
+            bar_named(CONS_BAR, NC);
+        }
+        float2* part2 = reinterpret_cast<float2*>(P.colpart);
+        for (int j = tid; j < J; j += NC) {
+            float ss = comb[j];
+            for (int t = 1; t < HALF; ++t) ss += comb[t * Jp + j];
+            part2[(int64_t)b * Jp + j] = make_float2(Gs[j], ss);
+        }
+        OTA_BARRIER();
+        // G^1_j = G^0_j + log2 q^_j - log2(column sum of pi^(1/2)), one warp per column
+        {
+            const int gw = b * NCW + warp, nw = nb * NCW;
+            for (int j = gw; j < J; j += nw) {
+                float mm = -INFINITY;
+                for (int bb = lane; bb < nb; bb += 32) mm = fmaxf(mm, part2[(int64_t)bb * Jp + j].x);
+                mm = warp_max(mm);
+                double ss = 0.0;
+                if (mm > -INFINITY)
+                    for (int bb = lane; bb < nb; bb += 32) {
+                        const float2 o = part2[(int64_t)bb * Jp + j];
+                        if (o.x > -INFINITY) ss += (double)o.y * (double)ex2(o.x - mm);
+                    }
+                ss = warp_sum(ss);
+                if (lane == 0) {
+                    if (!(ss > 0.0) || !isfinite(ss)) {
+                        atomicCAS(status, DEV_OK, DEV_ENUMERIC);
+                    } else {
+                        const double Gu = (double)(float)P.G[j];
+                        P.G[Jp + j] = Gu + LQ[j] - ((double)mm + log2(ss));
+                    }
+                }
+            }
+        }
+        OTA_BARRIER_CHECK();
+        load_G_smem(P.G + Jp, J, Jp, Gs, tid, NC);
+        bar_named(CONS_BAR, NC);
+    }
+
+    // ---- sweeps 2, 3, ...: one read of C and one ex2 per cell -----------------------------
+    for (int s = 2;; ++s) {
+        const float2* Fold = Fs + ((s - 1) & 1) * S.rmax;  // F'^(s-1)
+        float2* Fnew = Fs + (s & 1) * S.rmax;
+        float4 acc[VPT];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float errt = 0.f;  // every lane of a team holds the same value
+        for (int kb = 0; kb < nblk; ++kb) {
+            const int st = (int)(cseq % (uint32_t)S.stages);
+            const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
+            const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, g.abort);
+            const int lr0 = kb * S.rows_per_stage;
+            const int rows = min(S.rows_per_stage, nrow - lr0);
+            const float* stage = ring + (size_t)st * S.stage_floats;
+            for (int j = 0; ok && j < S.rpt; ++j) {
+                const int rr = tm.team + NTEAMS * j;
+                if (rr >= rows) break;
+                const int lr = lr0 + rr;
+                float4 x[VPT];
+                load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
+                const float2 F = Fold[lr];
+                float rs = 0.f;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const int col = 4 * (tm.tl + TT * v);
+                    if (chunk_inside<TW, VPT>(v) || col < J) {  // chunks past the row carry no mass
+                        float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float t = ex2(expo(F.x, F.y + comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
+                            comp(x[v], c) = t;
+                            rs += t;
+                        }
+                    } else {
+                        x[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+                rs = team_reduce<TW, float, false>(rs, red, NTEAMS, tm, par);
+                const float ph = Ps[lr];
+                // every lane forms the update (no divergent branch); one lane stores it
+                const float2 Fn = df_sub(F, log2_corr(rs));
+                if (tm.tl == 0) Fnew[lr] = Fn;
+                errt = fmaf(ph, fabsf(rs - 1.0f), errt);
+                const float d = __fdividef(ph, rs);
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    acc[v].x = fmaf(x[v].x, d, acc[v].x);
+                    acc[v].y = fmaf(x[v].y, d, acc[v].y);
+                    acc[v].z = fmaf(x[v].z, d, acc[v].z);
+                    acc[v].w = fmaf(x[v].w, d, acc[v].w);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+            ++cseq;
+        }
+        // CTA combine of the column partials in a fixed order: the first half of the teams
+        // stores, the second half adds its partial onto slot team - NTEAMS/2, then the slots
+        // are summed in order (the buffer holds NTEAMS/2 rows).
+        constexpr int HALF = (NTEAMS + 1) / 2;
+        if (tm.team < HALF) {
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int col = 4 * (tm.tl + TT * v);
+                if (col < Jp) *reinterpret_cast<float4*>(comb + tm.team * Jp + col) = acc[v];
+            }
+        }
+        if (tm.tl == 0) errf[tm.team] = errt;
+        bar_named(CONS_BAR, NC);
+        if (tm.team >= HALF) {
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int col = 4 * (tm.tl + TT * v);
+                if (col < Jp) {
+                    float4* d = reinterpret_cast<float4*>(comb + (tm.team - HALF) * Jp + col);
+                    float4 o = *d;
+                    o.x += acc[v].x;
+                    o.y += acc[v].y;
+                    o.z += acc[v].z;
+                    o.w += acc[v].w;
+                    *d = o;
+                }
+            }
+        }
+        bar_named(CONS_BAR, NC);
+        for (int j = tid; j < J; j += NC) {
+            float sum = comb[j];
+            for (int t = 1; t < HALF; ++t) sum += comb[t * Jp + j];
+            P.colpart[(int64_t)b * Jp + j] = sum;
+        }
+        float2* errp = reinterpret_cast<float2*>(P.errpart);
+        if (tid == 0) {
+            float2 e = make_float2(errf[0], 0.f);
+            for (int t = 1; t < NTEAMS; ++t) e = df_add(e, errf[t]);
+            errp[b] = e;
+        }
+        OTA_BARRIER();
+        // Loop test on pi^(s-1) (warp 0; every CTA forms the same total in the same order)
+        // while the other warps already form G^s into the other buffer: G^(s-1) stays intact
+        // for a stop.  All sums here are FP32 pairs: no FP64 in the per-sweep path.
+        if (warp == 0) {
+            float2 e = make_float2(0.f, 0.f);
+            for (int bb = lane; bb < nb; bb += 32) e = df_add2(e, errp[bb]);
+            e = warp_sum_df(e);
+            if (lane == 0) {
+                const double ed = (double)e.x + (double)e.y;
+                const int stop = (ed <= P.tol) || (s - 1 >= P.max_iter);
+                s_dec = stop;
+                if (stop && b == 0) {
+                    P.st->iters = s - 1;
+                    P.st->err = ed;
+                    P.st->converged = (ed <= P.tol);
+                }
+            }
+        }
+        {
+            const double* Gold = P.G + ((s - 1) & 1) * Jp;
+            double* Gnew = P.G + (s & 1) * Jp;
+            const int gw = b * (NCW - 1) + (warp - 1), nw = nb * (NCW - 1);
+            for (int j = gw; warp > 0 && j < J; j += nw) {
+                float2 sum = make_float2(0.f, 0.f);
+                for (int bb = lane; bb < nb; bb += 32) sum = df_add(sum, P.colpart[(int64_t)bb * Jp + j]);
+                sum = warp_sum_df(sum);
+                if (lane == 0) {
+                    if (!(sum.x > 0.f) || !isfinite(sum.x)) {
+                        atomicCAS(status, DEV_OK, DEV_ENUMERIC);
+                    } else {
+                        const float2 ls = df_log2(sum);  // log2 s_j = ls.x + ls.y
+                        const float Gu = (float)Gold[j];
+                        Gnew[j] = ((double)Gu - (double)ls.x) + (LQ[j] - (double)ls.y);
+                    }
+                }
+            }
+        }
+        bar_named(CONS_BAR, NC);
+        if (s_dec) {
+            if (P.F_out)
+                for (int r = tid; r < nrow; r += NC) P.F_out[r0 + r] = Fold[r];
+            *ret_par = (s - 1) & 1;
+            if (tid == 0) s_stop = 1;
+            return true;
+        }
+        OTA_BARRIER_CHECK();
+        load_G_smem(P.G + (s & 1) * Jp, J, Jp, Gs, tid, NC);
+        bar_named(CONS_BAR, NC);
+    }
+#undef OTA_BARRIER_CHECK
+#undef OTA_BARRIER
+}
+
+}  // namespace ota
