@@ -331,18 +331,24 @@ ot_status ot_assoc_batch_wait(ot_assoc_batch* b, void* stream, ot_assoc_instance
 
 void ot_assoc_batch_destroy(ot_assoc_batch* b);
 
-/* Measure, for every size bucket present in inst[0..n), the candidate (group size, stage
- * size) pairs on those instances (iters iterations each, outputs to scratch, the callers'
- * buffers untouched) and store the fastest per bucket in the context's tuning table. */
+/* Autotune the tuning table on a batch: bucket by bucket, time the whole batch (iters
+ * iterations, outputs to scratch, the callers' buffers untouched) with the bucket's
+ * instances on the candidate (group size, stage size) pairs, keep the fastest. */
 ot_status ot_assoc_autotune(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int32_t n,
                             int32_t iters, void* stream);
 
-/* Tuning table access: bucket b in [0, 15) (cells class * 3 + J class); gsize 0 = untuned. */
+/* Tuning table: per instance size bucket b in [0, 15) (cells class * 3 + J class), the
+ * schedule (CTAs per instance group, a divisor of the SM count; 0 = untuned: a model picks
+ * it from the instance's estimated sweep time) and the tile (stage size in bytes, rows of
+ * C per bulk copy; 0 = 24 KB); rate = cells * iterations / s of the batch it was tuned on.
+ * The choice depends on the instance alone, so an instance's result is the same bit for
+ * bit in any batch. */
 ot_status ot_assoc_tuning_get(const ot_assoc_ctx* ctx, int32_t bucket, int32_t* gsize,
                               int32_t* stage_bytes, double* rate);
 ot_status ot_assoc_tuning_set(ot_assoc_ctx* ctx, int32_t bucket, int32_t gsize, int32_t stage_bytes);
 /* Size bucket of an I x J instance. */
 int32_t ot_assoc_bucket(int64_t I, int32_t J);
+
 
 #ifdef __cplusplus
 }

@@ -540,6 +540,7 @@ def bucket(I: int, J: int) -> int:
     return int(lib().ot_assoc_bucket(int(I), int(J)))
 
 
+
 Context.solve_batched = _ctx_solve_batched
 Context.autotune = _ctx_autotune
 Context.tuning = _ctx_tuning

@@ -31,14 +31,12 @@ namespace ota {
 static constexpr int BT_NCW = Cons<1>::NCW;  // consumer warps (one-warp teams)
 static constexpr int BT_NT = Cons<1>::NT;    // + the producer warp
 static constexpr int BT_NW = BT_NT / 32;
-static constexpr int BT_MAX_FIN_TEAMS = 8;
 
 // One instance as the kernel sees it (host-written).
 struct BInst {
     SolveParams P;  // C, ld, I, J, Jp, p, q, g_warm, k, k_hi, k_lo, tol, max_iter (scratch filled per group)
     StreamCfg S;    // stage geometry and shared-memory layout at this instance's group size
     int vpt;        // float4 chunks per lane (J4 <= 32 * vpt)
-    int fin_teams;  // finalize teams that fit next to the row potentials
     double eps_ln2;
     double* f_out;
     double* g_out;
@@ -53,8 +51,9 @@ struct BRes {
     int iters, converged, status, done;
 };
 
+// Instances planned for one group size, taken largest first from one queue.
 struct BPhase {
-    int gsize, ngroups, first, count;
+    int gsize, first, count;
 };
 
 // Scratch of one group (sized for the largest instance of its phase).
@@ -62,10 +61,12 @@ struct BGroup {
     DevScalars* sc;
     LoopState* ls;
     double* G;         // [3][Jp]
-    float* colpart;    // [gsize][2 * Jp]
-    double* errpart;   // [gsize] (x2)
-    double2* fpart;    // [gsize][Jp] finalize column partials
-    double* fred;      // [gsize][BT_NW][2] finalize totals per warp; then [gsize] row residuals
+    float* colpart;    // [V][2 * Jp]
+    double* errpart;   // [V] (x2)
+    double2* fpart;    // [V][Jp] finalize column partials
+    double* fred;      // [gsize][BT_NW][2] finalize totals per warp; then [V] row residuals
+    int phase;         // the queue this group takes instances from
+    int first_cta;     // the group is CTAs [first_cta, first_cta + gsize)
 };
 
 struct BCtl {
@@ -79,9 +80,9 @@ struct BatchParams {
     BRes* res;
     const int* order;  // instance indices, phase by phase (largest first within a phase)
     const BPhase* phases;
-    int nphases;
-    const BGroup* groups;  // phase-major
-    const int* goff;       // first group of each phase
+    const BGroup* groups;
+    const int* cta_map;    // [nrounds][grid]: the group of each CTA in each round, or -1
+    int nrounds;
     BCtl* ctl;
     unsigned* gbar;        // per group (all phases): barrier counter
     int* gcur;             // per group: the instance index the leader fetched
@@ -102,100 +103,23 @@ __device__ __forceinline__ bool group_sync(unsigned* bar, unsigned nb, unsigned*
     return grid_barrier(bar, target, abort, spin);
 }
 
-// Finalize one instance on the group's rows (all threads of the CTA; the producer is idle).
-// Teams of one warp walk the CTA's rows; each lane adds p^ t and p^ C t of its cells, row by
-// row, into its team's FP32-pair accumulators in shared memory (the stage ring's space; each
-// lane owns its columns); CTAs combine teams in order and the group combines CTAs in order,
-// in FP64.
-template <int VPT>
-__device__ __forceinline__ bool bt_finalize(const BInst& D, const SolveParams& P, const BGroup& grp, int rank, int gsize,
-                            int64_t r0, int64_t r1, int par, unsigned char* dyn, unsigned* gbar, unsigned* s_gen,
-                            int* abort, long long spin, BRes* out) {
-    const StreamCfg& S = D.S;
+// Finish one instance after the solver's finalize sweep (which left per-CTA FP64 column
+// partials and row residuals in the group's scratch): one warp per column over the group's
+// CTAs in order, then the group's leader forms the totals.
+__device__ __forceinline__ bool bt_finalize(const BInst& D, const SolveParams& P, const BGroup& grp, int rank,
+                                            int gsize, int par, unsigned* gbar, unsigned* s_gen, int* abort,
+                                            long long spin, BRes* out) {
     const int J = P.J, Jp = P.Jp;
-    const int NTM = D.fin_teams;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* accs = reinterpret_cast<float4*>(dyn + S.off_ring);  // [NTM][Jp]
-    const float2* Fr = reinterpret_cast<const float2*>(dyn + S.off_F) + par * S.rmax;
     const double* Gk = P.G + par * Jp;
-    __shared__ float s_err[BT_NW];
-    for (int q = threadIdx.x; q < NTM * Jp; q += blockDim.x) accs[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    const float inv_sp_f = P.sc->inv_sp_f;
-    if (warp < NTM) {
-        float4* myacc = accs + (size_t)warp * Jp;
-        float4 g[VPT];
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            const int col = 4 * (lane + 32 * v);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) comp(g[v], c) = (col + c < J) ? (float)Gk[col + c] : 0.0f;
-        }
-        float errt = 0.f;
-        // no prefetch of the next row: the registers are needed (13 warps: 128 per thread);
-        // the loads of all teams in flight still cover the memory latency
-        for (int64_t i = r0 + warp; i < r1; i += NTM) {
-            float4 x[VPT];
-            load_row<1, VPT>(P.C + i * P.ld, J, lane, x);
-            const float2 F = Fr[i - r0];
-            const float pf = __ldg(P.p + i);
-            const float phf = pf * inv_sp_f;
-            float rs = 0.f;
-#pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const int col = 4 * (lane + 32 * v);
-                if (col < J) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (col + c < J) {
-                            const float cost = comp(x[v], c);
-                            const float t = ex2(expo(F.x, F.y + comp(g[v], c), cost, P.k_hi, P.k_lo));
-                            const float ct = t > 0.f ? cost * t : 0.f;
-                            rs += t;
-                            float4 a = myacc[col + c];
-                            const float2 s2 = df_add(make_float2(a.x, a.y), phf * t);
-                            const float2 r2 = df_add(make_float2(a.z, a.w), phf * ct);
-                            myacc[col + c] = make_float4(s2.x, s2.y, r2.x, r2.y);
-                            if (D.pi) D.pi[i * D.pi_ld + col + c] = pf * t;
-                        }
-                    }
-                }
-            }
-            float se = 0.f;
-            warp_sum_pair(rs, se);
-            errt = fmaf(phf, fabsf((rs - 1.0f) + se), errt);
-            if (lane == 0) D.f_out[i] = D.eps_ln2 * ((double)F.x + (double)F.y + log2((double)pf));
-        }
-        if (lane == 0) s_err[warp] = errt;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < J; j += blockDim.x) {
-        float4 a = accs[j];
-        float2 s = make_float2(a.x, a.y), r = make_float2(a.z, a.w);
-        for (int t = 1; t < NTM; ++t) {
-            const float4 o = accs[(size_t)t * Jp + j];
-            s = df_add2(s, make_float2(o.x, o.y));
-            r = df_add2(r, make_float2(o.z, o.w));
-        }
-        grp.fpart[(int64_t)rank * Jp + j] = make_double2((double)s.x + (double)s.y, (double)r.x + (double)r.y);
-    }
-    double* rowerr = grp.fred + (size_t)gsize * BT_NW * 2;
-    if (threadIdx.x == 0) {
-        float2 e = make_float2(s_err[0], 0.f);
-        for (int t = 1; t < NTM; ++t) e = df_add(e, s_err[t]);
-        rowerr[rank] = (double)e.x + (double)e.y;
-    }
-    // the next instance's bulk copies write where the accumulators were
-    fence_proxy_async_smem();
     if (!group_sync(gbar, gsize, s_gen, abort, spin)) return false;
-    // columns: one warp per column over the group's CTAs
     {
         const double inv_sq = P.sc->inv_sq, sp = P.sc->sp;
         double ec = 0.0, co = 0.0;
         const int gw = rank * BT_NW + warp, nw = gsize * BT_NW;
         for (int j = gw; j < J; j += nw) {
             double s = 0.0, r = 0.0;
-            for (int bb = lane; bb < gsize; bb += 32) {
+            for (int bb = lane; bb < P.V; bb += 32) {
                 const double2 v = grp.fpart[(int64_t)bb * Jp + j];
                 s += v.x;
                 r += v.y;
@@ -216,12 +140,13 @@ __device__ __forceinline__ bool bt_finalize(const BInst& D, const SolveParams& P
     }
     if (!group_sync(gbar, gsize, s_gen, abort, spin)) return false;
     if (rank == 0 && threadIdx.x == 0) {
+        const double* rowerr = grp.fred + (size_t)gsize * BT_NW * 2;
         double ec = 0.0, co = 0.0, er = 0.0;
         for (int k = 0; k < gsize * BT_NW; ++k) {
             ec += grp.fred[2 * k];
             co += grp.fred[2 * k + 1];
         }
-        for (int k = 0; k < gsize; ++k) er += rowerr[k];
+        for (int k = 0; k < P.V; ++k) er += rowerr[k];
         out->cost = co * P.sc->sp;
         out->err_row = er;
         out->err_col = ec;
@@ -248,6 +173,12 @@ __device__ __forceinline__ bool bt_instance(const BatchParams& B, int ii, const 
     P.F_out = nullptr;
     P.input_bad = nullptr;
     P.spin = B.spin;
+    P.fpart = grp.fpart;
+    P.epart = grp.fred + (size_t)gsize * BT_NW * 2;
+    P.pi = D.pi;
+    P.pi_ld = D.pi_ld;
+    P.f_nat = D.f_out;
+    P.eps_ln2 = D.eps_ln2;
     const StreamCfg S = D.S;
     uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
     uint64_t* empty = full + MAX_STAGES;
@@ -255,7 +186,7 @@ __device__ __forceinline__ bool bt_instance(const BatchParams& B, int ii, const 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int* abort = &B.ctl->abort;
     int64_t r0, r1;
-    cta_rows(P.I, S.rows_per_stage, rank, gsize, &r0, &r1);
+    cta_rows(P.I, S.rows_per_stage, P.V, rank, gsize, &r0, &r1);
     if (threadIdx.x == 0) {
         for (int s = 0; s < *s_nbar; ++s) {
             mbar_inval(&full[s]);
@@ -297,8 +228,7 @@ __device__ __forceinline__ bool bt_instance(const BatchParams& B, int ii, const 
         }
         return true;
     }
-    return bt_finalize<VPT>(D, P, grp, rank, gsize, r0, r1, s_res - 1, dyn, gbar, s_gen, abort, B.spin,
-                            B.res + ii);
+    return bt_finalize(D, P, grp, rank, gsize, s_res - 1, gbar, s_gen, abort, B.spin, B.res + ii);
 }
 
 __global__ void __launch_bounds__(BT_NT, 1) sk_batch(BatchParams B) {
@@ -311,12 +241,13 @@ __global__ void __launch_bounds__(BT_NT, 1) sk_batch(BatchParams B) {
         s_nbar = 0;
     }
     __syncthreads();
-    for (int ph = 0; ph < B.nphases; ++ph) {
-        const BPhase PH = B.phases[ph];
-        const int grp_i = blockIdx.x / PH.gsize, rank = blockIdx.x % PH.gsize;
-        if (grp_i < PH.ngroups) {
-            const int gi = B.goff[ph] + grp_i;
+    for (int rd = 0; rd < B.nrounds; ++rd) {
+        const int gi = B.cta_map[rd * gridDim.x + blockIdx.x];
+        if (gi >= 0) {
             const BGroup grp = B.groups[gi];
+            const int ph = grp.phase;
+            const BPhase PH = B.phases[ph];
+            const int rank = blockIdx.x - grp.first_cta;
             unsigned* gbar = B.gbar + gi;
             if (threadIdx.x == 0) s_gen = 0;
             for (;;) {
@@ -341,6 +272,7 @@ __global__ void __launch_bounds__(BT_NT, 1) sk_batch(BatchParams B) {
                 if (!go) return;
             }
         }
+        if (rd + 1 == B.nrounds) break;
         unsigned target = 0;
         if (threadIdx.x == 0) target = gridDim.x * ++s_ggen;
         if (!grid_barrier(&B.ctl->grid_bar, target, &B.ctl->abort, B.spin)) return;
@@ -358,44 +290,8 @@ constexpr int MAX_J_BATCH = 1024;              // one-warp teams: J4 <= 32 * 8
 int vpt_for(int J) { return std::max(1, (int)((round_up(J, 4) / 4 + 31) / 32)); }
 
 // Stage geometry and shared-memory layout of one instance solved by nb CTAs.
-bool plan_stream(int64_t I, int Jp, int64_t ld, int nb, int stage_target, StreamCfg* S, size_t* smem,
-                 int* fin_teams) {
-    constexpr int NTEAMS = BT_NCW;
-    const size_t comb = (size_t)((NTEAMS + 1) / 2) * Jp * sizeof(float);
-    const size_t row_bytes = (size_t)ld * sizeof(float);
-    int rpt = (int)std::max<size_t>(1, (size_t)stage_target / ((size_t)NTEAMS * row_bytes));
-    for (;;) {
-        const int rs = NTEAMS * rpt;
-        const int64_t blocks = (I + rs - 1) / rs;
-        const int64_t bpc = (blocks + nb - 1) / nb;
-        const int rmax = (int)std::min<int64_t>(bpc * rs, I);
-        const size_t off_G = round_up(SMEM_HDR + comb, 16);
-        const size_t off_F = round_up(off_G + (size_t)Jp * sizeof(float), 16);
-        const size_t off_P = off_F + (size_t)2 * rmax * sizeof(float2);
-        const size_t off_ring = round_up(off_P + (size_t)rmax * sizeof(float), 128);
-        const size_t stage = (size_t)rs * row_bytes;
-        const int stages =
-            off_ring < SMEM_BUDGET ? (int)std::min<size_t>(MAX_STAGES, (SMEM_BUDGET - off_ring) / stage) : 0;
-        int ft = 0;
-        for (int t = BT_MAX_FIN_TEAMS; t >= 1 && !ft; t /= 2)
-            if (off_ring + (size_t)t * Jp * sizeof(float4) <= SMEM_BUDGET) ft = t;
-        if (ft && (stages >= 3 || (stages >= 2 && rpt == 1))) {
-            S->rpt = rpt;
-            S->rows_per_stage = rs;
-            S->stages = stages;
-            S->stage_floats = (int)(stage / sizeof(float));
-            S->rmax = rmax;
-            S->off_G = (int)off_G;
-            S->off_F = (int)off_F;
-            S->off_P = (int)off_P;
-            S->off_ring = (int)off_ring;
-            *smem = off_ring + std::max((size_t)stages * stage, (size_t)ft * Jp * sizeof(float4));
-            *fin_teams = ft;
-            return true;
-        }
-        if (rpt == 1) return false;
-        rpt = std::max(1, rpt / 2);
-    }
+bool plan_stream(int64_t I, int Jp, int64_t ld, int nb, int stage_target, StreamCfg* S, size_t* smem, int* V) {
+    return plan_stage(BT_NCW, I, Jp, ld, nb, stage_target, SMEM_BUDGET, S, smem, V);
 }
 
 std::vector<int> divisors(int n) {
@@ -405,13 +301,39 @@ std::vector<int> divisors(int n) {
     return d;
 }
 
-// Default schedule before tuning: about 2^18 cells per CTA, at most one row block per CTA.
-int default_gsize(int64_t I, int J, int num_sms) {
-    const double cells = (double)I * J;
-    const int64_t blocks = (I + BT_NCW - 1) / BT_NCW;
+// Schedule model (used before tuning and to pick the candidates the tuner times): one sweep
+// of instance i on d CTAs takes the longer of streaming its cells at a CTA's share of HBM
+// bandwidth and walking its rows at the consumer warps' row rate, plus the group barriers.
+constexpr double BW_CTA = 40e9;       // bytes/s one CTA streams with all SMs busy
+constexpr double ROW_TIME = 0.5e-6;   // s per row per warp (latency of a row's chain)
+double sweep_time(int64_t I, int J, int d) {
+    const double stream = 4.0 * (double)I * J / (d * BW_CTA);
+    const double rows = std::ceil((double)I / d) * ROW_TIME / BT_NCW;
+    const double bar = d > 1 ? 3e-6 + 0.02e-6 * d : 0.5e-6;
+    return std::max(stream, rows) + bar;
+}
+
+// Group size of a batch: the divisor of the SM count that minimises the estimated makespan
+// of a largest-first queue over nsm / d groups (every instance taken at the same number of
+// sweeps).  Results do not depend on it: every reduction runs over the instances' own row
+// partitions.
+int model_gsize(const std::vector<ot_assoc_instance>& v, int num_sms) {
     int best = 1;
-    for (int d : divisors(num_sms))
-        if (d <= cells / 262144.0 && d <= blocks) best = d;
+    double best_t = 1e300;
+    for (int d : divisors(num_sms)) {
+        const int ng = num_sms / d;
+        std::vector<double> t;
+        t.reserve(v.size());
+        for (const auto& a : v) t.push_back(sweep_time(a.I, a.J, d));
+        std::sort(t.begin(), t.end(), std::greater<double>());
+        std::vector<double> load(ng, 0.0);  // greedy list schedule, largest first
+        for (double x : t) *std::min_element(load.begin(), load.end()) += x;
+        const double m = *std::max_element(load.begin(), load.end());
+        if (m < best_t * 0.98) {  // prefer smaller groups unless clearly slower
+            best_t = m;
+            best = d;
+        }
+    }
     return best;
 }
 
@@ -443,7 +365,6 @@ struct ot_assoc_batch {
     std::vector<int> h_order;
     std::vector<ota::BPhase> h_phases;
     std::vector<ota::BGroup> h_groups;
-    std::vector<int> h_goff;
     // device memory (one allocation)
     void* dmem = nullptr;
     size_t dbytes = 0;
@@ -520,19 +441,13 @@ static void batch_free(ot_assoc_batch* b) {
     b->h_res = nullptr;
 }
 
-// Group size and stage target of an instance: the tuned entry of its bucket, else defaults.
-static void choose(const ot_assoc_ctx* ctx, int64_t I, int J, int* gsize, int* stage) {
-    const int bk = batch_bucket(I, J);
-    const TuneEntry& t = ctx->tune[bk];
-    *gsize = t.gsize > 0 ? t.gsize : default_gsize(I, J, ctx->num_sms);
+// Stage target and group size of an instance: the tuned entry of its size bucket, else 24 KB
+// and the batch's modelled group size.  The stage size fixes the instance's arithmetic (its
+// rows per stage and row partitions); the group size only which CTAs do the work.
+static void choose(const ot_assoc_ctx* ctx, int64_t I, int J, int g_batch, int* gsize, int* stage) {
+    const TuneEntry& t = ctx->tune[batch_bucket(I, J)];
     *stage = t.stage > 0 ? t.stage : 24576;
-    const int64_t blocks = (I + BT_NCW - 1) / BT_NCW;
-    while (*gsize > 1 && *gsize > blocks) {  // every CTA of a group owns at least one row block
-        int next = 1;
-        for (int d : divisors(ctx->num_sms))
-            if (d < *gsize) next = d;
-        *gsize = next;
-    }
+    *gsize = t.gsize > 0 ? t.gsize : g_batch;
 }
 
 // Plan the schedule and device layout; forced_gsize / forced_stage (> 0) override the choice
@@ -544,21 +459,21 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
     std::vector<int> gs(n), stg(n);
     std::vector<BInst> d(n);
     size_t smem = 0;
+    const int g_batch = model_gsize(b->inst, nsm);
     for (int k = 0; k < n; ++k) {
         const ot_assoc_instance& a = b->inst[k];
         int g, st;
-        choose(ctx, a.I, a.J, &g, &st);
+        choose(ctx, a.I, a.J, g_batch, &g, &st);
         if (forced_gsize > 0) g = forced_gsize;
         if (forced_stage > 0) st = forced_stage;
         std::memset(&d[k], 0, sizeof(BInst));
         fill_values(&d[k], a);
         d[k].vpt = vpt_for(a.J);
         size_t sm = 0;
-        int ft = 0;
         // grow the group until the CTA's share of the rows fits next to two stages
         bool ok = false;
         for (;;) {
-            if (plan_stream(a.I, d[k].P.Jp, d[k].P.ld, g, st, &d[k].S, &sm, &ft)) {
+            if (plan_stream(a.I, d[k].P.Jp, d[k].P.ld, g, st, &d[k].S, &sm, &d[k].P.V)) {
                 ok = true;
                 break;
             }
@@ -573,7 +488,6 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
         }
         if (!ok) return set_error(ctx, OT_EUNSUPPORTED, "instance %d (I=%lld J=%d) does not fit the shared memory", k,
                                   (long long)a.I, a.J);
-        d[k].fin_teams = ft;
         gs[k] = g;
         stg[k] = st;
         smem = std::max(smem, sm);
@@ -585,33 +499,77 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
     if ((int)sizes.size() > 16) return set_error(ctx, OT_EUNSUPPORTED, "too many phases");
     b->h_phases.clear();
     b->h_order.clear();
-    b->h_goff.clear();
-    int ngroups_total = 0;
-    std::vector<size_t> phase_jp, phase_gsz;
+    std::vector<size_t> phase_jp, phase_v;
+    std::vector<double> phase_work;  // estimated CTA-seconds per sweep
     for (int g : sizes) {
         BPhase ph;
         ph.gsize = g;
-        ph.ngroups = nsm / g;
         ph.first = (int)b->h_order.size();
         std::vector<int> idx;
-        int jpmax = 4;
+        int jpmax = 4, vmax = 1;
+        double w = 0.0;
         for (int k = 0; k < n; ++k)
             if (gs[k] == g) {
                 idx.push_back(k);
                 jpmax = std::max(jpmax, d[k].P.Jp);
+                vmax = std::max(vmax, d[k].P.V);
+                w += sweep_time(b->inst[k].I, b->inst[k].J, g) * g;
             }
         std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
             return (double)b->inst[x].I * b->inst[x].J > (double)b->inst[y].I * b->inst[y].J;
         });
         ph.count = (int)idx.size();
         b->h_order.insert(b->h_order.end(), idx.begin(), idx.end());
-        b->h_goff.push_back(ngroups_total);
-        ngroups_total += ph.ngroups;
         b->h_phases.push_back(ph);
         phase_jp.push_back((size_t)jpmax);
-        phase_gsz.push_back((size_t)g);
+        phase_v.push_back((size_t)vmax);
+        phase_work.push_back(w);
     }
-    // device layout: [inst][res][ctl][gbar][gcur][order][phases][goff][groups][group scratch...]
+    // rounds: phases that fit side by side (one group each) run at the same time; within a
+    // round the remaining CTAs go, one group at a time, to the phase with the most work per
+    // CTA (never more groups than the phase has instances)
+    struct GroupPlan {
+        int phase, first_cta;
+    };
+    std::vector<GroupPlan> gplan;
+    std::vector<int> cta_map;
+    int nrounds = 0;
+    for (size_t p0 = 0; p0 < b->h_phases.size();) {
+        size_t p1 = p0;
+        int used = 0;
+        while (p1 < b->h_phases.size() && used + b->h_phases[p1].gsize <= nsm) used += b->h_phases[p1++].gsize;
+        std::vector<int> ngrp(p1 - p0, 1);
+        for (;;) {
+            int best = -1;
+            double best_load = 0.0;
+            for (size_t q = p0; q < p1; ++q) {
+                const BPhase& ph = b->h_phases[q];
+                if (used + ph.gsize > nsm || ngrp[q - p0] >= ph.count) continue;
+                const double load = phase_work[q] / (ngrp[q - p0] * ph.gsize);
+                if (load > best_load) {
+                    best_load = load;
+                    best = (int)q;
+                }
+            }
+            if (best < 0) break;
+            ++ngrp[best - p0];
+            used += b->h_phases[best].gsize;
+        }
+        std::vector<int> map(nsm, -1);
+        int cta = 0;
+        for (size_t q = p0; q < p1; ++q)
+            for (int r = 0; r < ngrp[q - p0]; ++r) {
+                const int gi = (int)gplan.size();
+                gplan.push_back({(int)q, cta});
+                for (int c = 0; c < b->h_phases[q].gsize; ++c) map[cta + c] = gi;
+                cta += b->h_phases[q].gsize;
+            }
+        cta_map.insert(cta_map.end(), map.begin(), map.end());
+        ++nrounds;
+        p0 = p1;
+    }
+    const int ngroups_total = (int)gplan.size();
+    // device layout: [inst][res][ctl][gbar][gcur][order][phases][cta_map][groups][group scratch...]
     auto al = [](size_t x) { return (size_t)round_up((int64_t)x, 256); };
     size_t off = 0;
     const size_t o_inst = off;
@@ -629,24 +587,18 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
     off = al(off + sizeof(int) * n);
     const size_t o_phases = off;
     off = al(off + sizeof(BPhase) * b->h_phases.size());
-    const size_t o_goff = off;
-    off = al(off + sizeof(int) * b->h_goff.size());
+    const size_t o_map = off;
+    off = al(off + sizeof(int) * cta_map.size());
     const size_t o_groups = off;
     off = al(off + sizeof(BGroup) * ngroups_total);
     std::vector<size_t> g_off(ngroups_total);
-    std::vector<size_t> g_sizes(ngroups_total);
-    {
-        int gi = 0;
-        for (size_t p = 0; p < b->h_phases.size(); ++p) {
-            const size_t Jp = phase_jp[p], nb = phase_gsz[p];
-            const size_t bytes = 1024 + al(3 * Jp * 8) + al(nb * 2 * Jp * 4) + al(nb * 16) + al(nb * Jp * 16) +
-                                 al(nb * BT_NW * 16 + nb * 8);
-            for (int q = 0; q < b->h_phases[p].ngroups; ++q, ++gi) {
-                g_off[gi] = off;
-                g_sizes[gi] = bytes;
-                off = al(off + bytes);
-            }
-        }
+    for (int gi = 0; gi < ngroups_total; ++gi) {
+        const size_t Jp = phase_jp[gplan[gi].phase], nb = (size_t)b->h_phases[gplan[gi].phase].gsize;
+        const size_t nv = phase_v[gplan[gi].phase];
+        const size_t bytes = 1024 + al(3 * Jp * 8) + al(nv * 2 * Jp * 4) + al(nv * 16) + al(nv * Jp * 16) +
+                             al(nb * BT_NW * 16 + nv * 8);
+        g_off[gi] = off;
+        off = al(off + bytes);
     }
     const size_t total = off;
     // (re)allocate
@@ -671,27 +623,24 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
     b->d_gcur = (int*)(base + o_gcur);
     b->zero_bytes = zero_end - o_res;
     b->h_groups.resize(ngroups_total);
-    {
-        int gi = 0;
-        for (size_t p = 0; p < b->h_phases.size(); ++p) {
-            const size_t Jp = phase_jp[p], nb = phase_gsz[p];
-            for (int q = 0; q < b->h_phases[p].ngroups; ++q, ++gi) {
-                char* g = base + g_off[gi];
-                BGroup& G = b->h_groups[gi];
-                G.sc = (DevScalars*)g;
-                G.ls = (LoopState*)(g + 512);
-                size_t o = 1024;
-                G.G = (double*)(g + o);
-                o += al(3 * Jp * 8);
-                G.colpart = (float*)(g + o);
-                o += al(nb * 2 * Jp * 4);
-                G.errpart = (double*)(g + o);
-                o += al(nb * 16);
-                G.fpart = (double2*)(g + o);
-                o += al(nb * Jp * 16);
-                G.fred = (double*)(g + o);
-            }
-        }
+    for (int gi = 0; gi < ngroups_total; ++gi) {
+        const size_t Jp = phase_jp[gplan[gi].phase], nv = phase_v[gplan[gi].phase];
+        char* g = base + g_off[gi];
+        BGroup& G = b->h_groups[gi];
+        G.sc = (DevScalars*)g;
+        G.ls = (LoopState*)(g + 512);
+        size_t o = 1024;
+        G.G = (double*)(g + o);
+        o += al(3 * Jp * 8);
+        G.colpart = (float*)(g + o);
+        o += al(nv * 2 * Jp * 4);
+        G.errpart = (double*)(g + o);
+        o += al(nv * 16);
+        G.fpart = (double2*)(g + o);
+        o += al(nv * Jp * 16);
+        G.fred = (double*)(g + o);
+        G.phase = gplan[gi].phase;
+        G.first_cta = gplan[gi].first_cta;
     }
     std::memcpy(b->h_inst, d.data(), sizeof(BInst) * n);
     e = cudaMemcpy(base + o_order, b->h_order.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
@@ -699,7 +648,7 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
         e = cudaMemcpy(base + o_phases, b->h_phases.data(), sizeof(BPhase) * b->h_phases.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(base + o_goff, b->h_goff.data(), sizeof(int) * b->h_goff.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(base + o_map, cta_map.data(), sizeof(int) * cta_map.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(base + o_groups, b->h_groups.data(), sizeof(BGroup) * ngroups_total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -711,9 +660,9 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
     BP.res = b->d_res;
     BP.order = (const int*)(base + o_order);
     BP.phases = (const BPhase*)(base + o_phases);
-    BP.nphases = (int)b->h_phases.size();
     BP.groups = (const BGroup*)(base + o_groups);
-    BP.goff = (const int*)(base + o_goff);
+    BP.cta_map = (const int*)(base + o_map);
+    BP.nrounds = nrounds;
     BP.ctl = b->d_ctl;
     BP.gbar = b->d_gbar;
     BP.gcur = b->d_gcur;
@@ -872,112 +821,123 @@ ot_status batch_set(ot_assoc_batch* b, int k, const ot_assoc_instance* a) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Autotuner.  For each size bucket present in `inst`, time the candidate (group size, stage
-// size) pairs on that bucket's instances (replicated so that every group of the phase has
-// work), with a fixed number of iterations and outputs sent to scratch, and keep the pair
-// with the highest cells * iterations / s.  Results go into the context's tuning table.
+// Autotuner.  Times the batch itself (a fixed number of iterations, tol = 0, outputs sent to
+// scratch so the callers' buffers are untouched).  Size bucket by bucket (largest total
+// work first), the bucket's instances try the group sizes around the current choice and
+// the stage sizes, the others keeping theirs; the fastest pair becomes the bucket's entry.
 // ------------------------------------------------------------------------------------------
+static ot_status time_batch(ot_assoc_ctx* ctx, const std::vector<ot_assoc_instance>& tb,
+                            const std::vector<TuneEntry>& trial, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                            float* ms_out) {
+    TuneEntry saved[TUNE_BUCKETS];
+    std::copy(ctx->tune, ctx->tune + TUNE_BUCKETS, saved);
+    std::copy(trial.begin(), trial.end(), ctx->tune);
+    ot_assoc_batch* b = nullptr;
+    ot_status st = batch_create(ctx, tb.data(), (int)tb.size(), OT_BATCH_NO_GRAPH, &b);
+    std::copy(saved, saved + TUNE_BUCKETS, ctx->tune);
+    if (st) return st;
+    float ms = 0.f;
+    st = batch_launch(b, s);  // warm-up
+    if (!st) st = batch_wait(b, s, nullptr);
+    if (!st) {
+        cudaEventRecord(e0, s);
+        st = batch_launch(b, s);
+        cudaEventRecord(e1, s);
+        if (!st) st = batch_wait(b, s, nullptr);
+        if (!st && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            st = set_error(ctx, OT_ECUDA, "autotune timing");
+        }
+    }
+    batch_destroy(b);
+    *ms_out = ms;
+    return st;
+}
+
 ot_status batch_autotune(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, int n, int iters, cudaStream_t s) {
     if (iters < 3) iters = 3;
-    std::vector<std::vector<int>> by_bucket(TUNE_BUCKETS);
+    std::vector<ot_assoc_instance> tb(inst, inst + n);
+    int64_t Isum = 0, Jsum = 0;
     for (int k = 0; k < n; ++k) {
         ot_status st = batch_check(ctx, inst[k], k);
         if (st) return st;
-        by_bucket[batch_bucket(inst[k].I, inst[k].J)].push_back(k);
+        Isum += round_up(inst[k].I, 32);
+        Jsum += round_up(inst[k].J, 32);
     }
-    const std::vector<int> divs = divisors(ctx->num_sms);
-    const int stages[3] = {12288, 24576, 49152};
+    ot_status st = OT_OK;
+    double* outbuf = (double*)scratch(ctx, SLOT_TUNE, sizeof(double) * (size_t)(Isum + Jsum), &st);
+    if (st) return st;
+    {
+        int64_t o = 0;
+        for (int k = 0; k < n; ++k) {
+            tb[k].f = outbuf + o;
+            o += round_up(inst[k].I, 32);
+            tb[k].g = outbuf + o;
+            o += round_up(inst[k].J, 32);
+            tb[k].rrh_load = nullptr;
+            tb[k].pi = nullptr;
+            tb[k].warm_start = 0;
+            tb[k].tol = 0.0;
+            tb[k].max_iter = iters;
+        }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
         if (e0) cudaEventDestroy(e0);
         return set_error(ctx, OT_ECUDA, "autotune events");
     }
-    ot_status result = OT_OK;
-    for (int bk = 0; bk < TUNE_BUCKETS && !result; ++bk) {
-        if (by_bucket[bk].empty()) continue;
-        // sample: up to 4 instances of the bucket; their largest Jp and I size the scratch
-        std::vector<int> sample(by_bucket[bk].begin(), by_bucket[bk].begin() + std::min<size_t>(4, by_bucket[bk].size()));
-        int64_t Imax = 0;
-        int Jmax = 0;
-        int64_t blocks_min = INT64_MAX;
-        for (int k : sample) {
-            Imax = std::max(Imax, inst[k].I);
-            Jmax = std::max(Jmax, inst[k].J);
-            blocks_min = std::min(blocks_min, (inst[k].I + BT_NCW - 1) / BT_NCW);
-        }
-        const int g0 = default_gsize(inst[sample[0]].I, inst[sample[0]].J, ctx->num_sms);
-        double best_rate = -1.0;
-        TuneEntry best = {};
-        for (int gsz : divs) {
-            if (gsz > blocks_min || gsz * 8 < g0 || gsz > g0 * 8) continue;
-            const int ngroups = ctx->num_sms / gsz;
-            const int reps = std::max<int>(2 * ngroups, (int)sample.size());
-            std::vector<ot_assoc_instance> tb(reps);
-            // outputs to scratch: f, g per replica (never the caller's buffers)
-            ot_status st = OT_OK;
-            const size_t per = (size_t)round_up(Imax, 32) + (size_t)round_up(Jmax, 32);
-            double* outbuf = (double*)scratch(ctx, SLOT_TUNE, sizeof(double) * per * reps, &st);
-            if (st) {
-                result = st;
-                break;
-            }
-            double cells_iter = 0.0;
-            for (int r = 0; r < reps; ++r) {
-                tb[r] = inst[sample[r % sample.size()]];
-                tb[r].f = outbuf + per * r;
-                tb[r].g = outbuf + per * r + round_up(Imax, 32);
-                tb[r].rrh_load = nullptr;
-                tb[r].pi = nullptr;
-                tb[r].warm_start = 0;
-                tb[r].tol = 0.0;
-                tb[r].max_iter = iters;
-                cells_iter += (double)tb[r].I * tb[r].J * (iters + 1);
-            }
+    // current choice of every bucket present (tuned entry, else the model at the bucket's
+    // largest instance and 24 KB stages), and the buckets' total work
+    std::vector<TuneEntry> cur(ctx->tune, ctx->tune + TUNE_BUCKETS);
+    std::vector<double> work(TUNE_BUCKETS, 0.0);
+    const int g_batch = model_gsize(tb, ctx->num_sms);
+    for (const auto& a : tb) {
+        const int bk = batch_bucket(a.I, a.J);
+        work[bk] += (double)a.I * a.J;
+        if (cur[bk].gsize <= 0) cur[bk].gsize = g_batch;
+        if (cur[bk].stage <= 0) cur[bk].stage = 24576;
+    }
+    std::vector<int> order;
+    for (int bk = 0; bk < TUNE_BUCKETS; ++bk)
+        if (work[bk] > 0) order.push_back(bk);
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    double cells_iter = 0.0;
+    for (const auto& a : tb) cells_iter += (double)a.I * a.J * (iters + 1);
+    const std::vector<int> divs = divisors(ctx->num_sms);
+    const int stages[3] = {12288, 24576, 49152};
+    for (int bk : order) {
+        if (st) break;
+        const int pos = (int)(std::find(divs.begin(), divs.end(), cur[bk].gsize) - divs.begin());
+        TuneEntry best = cur[bk];
+        float best_ms = 1e30f;
+        for (int q = std::max(0, pos - 2); q <= std::min((int)divs.size() - 1, pos + 2) && !st; ++q)
             for (int stg : stages) {
-                ot_assoc_batch* b = nullptr;
-                st = batch_create(ctx, tb.data(), reps, OT_BATCH_NO_GRAPH, &b, gsz, stg);
+                std::vector<TuneEntry> trial = cur;
+                trial[bk].gsize = divs[q];
+                trial[bk].stage = stg;
+                float ms = 0.f;
+                st = time_batch(ctx, tb, trial, s, e0, e1, &ms);
                 if (st == OT_EUNSUPPORTED) {
                     ctx->err.clear();
+                    st = OT_OK;
                     continue;
                 }
-                if (st) {
-                    result = st;
-                    break;
-                }
-                float ms = 0.f;
-                st = batch_launch(b, s);  // warm-up
-                if (!st) st = batch_wait(b, s, nullptr);
-                if (!st) {
-                    cudaEventRecord(e0, s);
-                    st = batch_launch(b, s);
-                    cudaEventRecord(e1, s);
-                    if (!st) st = batch_wait(b, s, nullptr);
-                    if (!st && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                        cudaGetLastError();
-                        ms = 0.f;
-                    }
-                }
-                batch_destroy(b);
-                if (st) {
-                    result = st;
-                    break;
-                }
-                const double rate = ms > 0.f ? cells_iter / (ms * 1e-3) : 0.0;
-                if (rate > best_rate) {
-                    best_rate = rate;
-                    best.gsize = gsz;
-                    best.stage = stg;
-                    best.rate = rate;
+                if (st) break;
+                if (ms > 0.f && ms < best_ms) {
+                    best_ms = ms;
+                    best = trial[bk];
                 }
             }
-            if (result) break;
+        if (!st && best_ms < 1e30f) {
+            best.rate = cells_iter / (best_ms * 1e-3);
+            cur[bk] = best;
+            ctx->tune[bk] = best;
         }
-        if (!result && best.gsize > 0) ctx->tune[bk] = best;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return result;
+    return st;
 }
 
 }  // namespace ota

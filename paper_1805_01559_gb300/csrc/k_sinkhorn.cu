@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve(SolveParams P, Strea
     float* ring = reinterpret_cast<float*>(dyn + S.off_ring);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t r0, r1;
-    cta_rows(P.I, S.rows_per_stage, blockIdx.x, gridDim.x, &r0, &r1);
+    cta_rows(P.I, S.rows_per_stage, P.V, blockIdx.x, gridDim.x, &r0, &r1);
     if (threadIdx.x == 0) {
         for (int s = 0; s < S.stages; ++s) {
             mbar_init(&full[s], 1);
@@ -70,169 +70,15 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve(SolveParams P, Strea
 }
 
 // ------------------------------------------------------------------------------------------
-// Finalize: plan, potentials in natural units, FP64 reductions of marginals, cost and loads.
-// Each CTA walks its rows RB at a time; thread t owns the column chunks t, t + NT_F, ...
-// (few columns per thread, so FP64 column accumulators are cheap).  Each thread sums its
-// few cells of a row in FP32, the warp reduces those with error-free two-sums, warps are
-// combined in FP64; column sums over a block of rows go from FP32 into the FP64
-// accumulators.
+// Finalize: the solver's last sweep (sk_finalize_sweep in sk_core.cuh) leaves per-CTA FP64
+// column partials (sum p^ t, sum p^ C t) and row residuals; these kernels finish the column
+// marginals, loads rho_j, potentials g in natural units, and the totals.
 // ------------------------------------------------------------------------------------------
-struct FinParams {
-    const float* C;
-    int64_t ld;
-    int64_t I;
-    int J;
-    int Jp;
-    const float* p;
-    const DevScalars* sc;
-    const LoopState* st;
-    const float2* F;
-    const double* G;
-    float k_hi, k_lo;
-    double eps_ln2;
-    float* pi;
-    int64_t pi_ld;
-    double* f_out;
-    double2* fpart;  // [nb][Jp] (sum p^ t, sum p^ C t)
-    double* epart;   // [nb] row residual
-};
-
-// Warp-per-row teams as in the solver.  Each lane keeps FP32 column sums of p^ t and
-// p^ C t for FIN_FLUSH rows, then adds them into its team's FP64 accumulators in shared
-// memory (each lane owns its columns: no conflicts); CTAs add their teams in team order.
-// The next row is loaded while the current one is worked on.
-static constexpr int FIN_FLUSH = 16;
-
-template <int TW, int VPT>
-__global__ void __launch_bounds__(NT_F, 1) sk_finalize(FinParams P) {
-    constexpr int TT = 32 * TW, NTEAMS = NT_F / TT;
-    extern __shared__ __align__(16) float4 accs[];  // [NTEAMS][Jp]: (sum p^ t, sum p^ C t) as pairs
-    __shared__ float red[2 * NTEAMS * TW * 2];
-    __shared__ float errs[NTEAMS];
-    if (P.st->status != DEV_OK) return;
-    const Team<TW> tm;
-    const int J = P.J, Jp = P.Jp;
-    const int nb = gridDim.x, b = blockIdx.x;
-    const int64_t r0 = P.I * b / nb, r1 = P.I * (b + 1) / nb;
-    const double* Gk = P.G + (P.st->iters & 1) * Jp;  // G^k of the returned plan
-    for (int q = threadIdx.x; q < NTEAMS * Jp; q += NT_F) accs[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    float4* myacc = accs + (size_t)tm.team * Jp;
-    float4 g[VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-        const int col = 4 * (tm.tl + TT * v);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) comp(g[v], c) = (col + c < J) ? (float)Gk[col + c] : 0.0f;
-    }
-    const float inv_sp_f = P.sc->inv_sp_f;
-    float cpi[VPT * 4], crho[VPT * 4];
-#pragma unroll
-    for (int q = 0; q < VPT * 4; ++q) cpi[q] = crho[q] = 0.f;
-    float errt = 0.f;
-    int par = 0, since = 0;
-    int64_t i = r0 + tm.team;
-    float4 xn[VPT];
-    if (i < r1) load_row<TW, VPT>(P.C + i * P.ld, J, tm.tl, xn);
-    for (; i < r1; i += NTEAMS) {
-        float4 x[VPT];
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) x[v] = xn[v];
-        const int64_t inext = i + NTEAMS;
-        if (inext < r1) load_row<TW, VPT>(P.C + inext * P.ld, J, tm.tl, xn);
-        const float2 F = P.F[i];
-        const float pf = __ldg(P.p + i);  // f_i itself is formed by sk_finalize_cols (all lanes busy)
-        const float phf = pf * inv_sp_f;
-        float rs = 0.f;
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            const int col = 4 * (tm.tl + TT * v);
-            if (col < J) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float cost = comp(x[v], c);
-                    const float t = ex2(expo(F.x, F.y + comp(g[v], c), cost, P.k_hi, P.k_lo));
-                    const float ct = t > 0.f ? cost * t : 0.f;
-                    rs += t;
-                    cpi[v * 4 + c] = fmaf(phf, t, cpi[v * 4 + c]);
-                    crho[v * 4 + c] = fmaf(phf, ct, crho[v * 4 + c]);
-                    if (P.pi && col + c < J) P.pi[i * P.pi_ld + col + c] = pf * t;
-                }
-            }
-        }
-        // error-free team sum of the row: warp pairs, then the team's warps in order
-        float se = 0.f;
-        warp_sum_pair(rs, se);
-        if constexpr (TW > 1) {
-            float2* r = reinterpret_cast<float2*>(red) + (par * NTEAMS + tm.team) * TW;
-            if (tm.lane == 0) r[tm.wit] = make_float2(rs, se);
-            bar_named(1 + tm.team, TT);
-            float2 a = r[0];
-            for (int w = 1; w < TW; ++w) a = df_add2(a, r[w]);
-            par ^= 1;
-            rs = a.x;
-            se = a.y;
-        }
-        // |row sum - 1| in FP32: rs - 1 is exact near 1, the pair's low part is added after
-        errt = fmaf(phf, fabsf((rs - 1.0f) + se), errt);
-        if (++since == FIN_FLUSH) {
-            since = 0;
-#pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const int col = 4 * (tm.tl + TT * v);
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (col + c < J) {
-                        float4 a = myacc[col + c];
-                        const float2 s2 = df_add(make_float2(a.x, a.y), cpi[v * 4 + c]);
-                        const float2 r2 = df_add(make_float2(a.z, a.w), crho[v * 4 + c]);
-                        myacc[col + c] = make_float4(s2.x, s2.y, r2.x, r2.y);
-                        cpi[v * 4 + c] = crho[v * 4 + c] = 0.f;
-                    }
-            }
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-        const int col = 4 * (tm.tl + TT * v);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (col + c < J) {
-                float4 a = myacc[col + c];
-                const float2 s2 = df_add(make_float2(a.x, a.y), cpi[v * 4 + c]);
-                const float2 r2 = df_add(make_float2(a.z, a.w), crho[v * 4 + c]);
-                myacc[col + c] = make_float4(s2.x, s2.y, r2.x, r2.y);
-            }
-    }
-    if (tm.tl == 0) errs[tm.team] = errt;
-    __syncthreads();
-    for (int j = threadIdx.x; j < J; j += NT_F) {
-        float4 a = accs[j];
-        float2 s = make_float2(a.x, a.y), r = make_float2(a.z, a.w);
-        for (int t = 1; t < NTEAMS; ++t) {
-            const float4 o = accs[(size_t)t * Jp + j];
-            s = df_add2(s, make_float2(o.x, o.y));
-            r = df_add2(r, make_float2(o.z, o.w));
-        }
-        P.fpart[(int64_t)b * Jp + j] = make_double2((double)s.x + (double)s.y, (double)r.x + (double)r.y);
-    }
-    if (threadIdx.x == 0) {
-        float2 e = make_float2(errs[0], 0.f);
-        for (int t = 1; t < NTEAMS; ++t) e = df_add(e, errs[t]);
-        P.epart[b] = (double)e.x + (double)e.y;
-    }
-}
-
 __global__ void sk_finalize_cols(const double2* __restrict__ fpart, int nb, int Jp, int J,
                                  const float* __restrict__ q, const DevScalars* sc,
                                  const LoopState* st, const double* G, double eps_ln2,
-                                 double* g_out, double* rrh_load, double2* cols, const float2* __restrict__ F,
-                                 const float* __restrict__ p, int64_t I, double* f_out) {
+                                 double* g_out, double* rrh_load, double2* cols) {
     if (st->status != DEV_OK) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 Fi = F[i];
-        f_out[i] = eps_ln2 * ((double)Fi.x + (double)Fi.y + log2((double)p[i]));
-    }
     G += (st->iters & 1) * Jp;  // G^k of the returned plan
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -302,13 +148,12 @@ namespace {
 
 struct Kernels {
     const void* solve;
-    const void* fin;
     int tw, vpt, ncw;
 };
 
 template <int TW, int VPT>
 Kernels kernels_for() {
-    return Kernels{(const void*)sk_solve<TW, VPT>, (const void*)sk_finalize<TW, VPT>, TW, VPT, Cons<TW>::NCW};
+    return Kernels{(const void*)sk_solve<TW, VPT>, TW, VPT, Cons<TW>::NCW};
 }
 
 // One-warp teams (TW = 1) get VPT = ceil(J4 / 32) exactly; chunk_inside() relies on it.
@@ -329,64 +174,27 @@ bool pick_kernels(int J, Kernels* k) {
     return true;
 }
 
-// Finalize launch: one CTA per SM (the team accumulators take most of the shared memory).
-ot_status plan_finalize(const Kernels& kk, int64_t I, int Jp, int num_sms, int cap, int* grid, size_t* smem) {
-    const int nteams = NT_F / (32 * kk.tw);
-    *smem = (size_t)nteams * Jp * sizeof(float4);
-    if (*smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kk.fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem) != cudaSuccess) {
-        cudaGetLastError();
-        return OT_ECUDA;
-    }
-    *grid = (int)std::max<int64_t>(1, std::min<int64_t>({(I + nteams - 1) / nteams, (int64_t)num_sms, (int64_t)cap}));
-    return OT_OK;
-}
-
-// Stage geometry, shared-memory layout and grid of the persistent kernel.
+// Stage geometry, shared-memory layout and grid of the persistent kernel: one CTA per row
+// partition (at most one per SM).
 struct LoopLaunch {
     StreamCfg cfg;
     size_t smem;
     int grid;
+    int V;
 };
 
 ot_status plan_solve(const Kernels& kk, int64_t I, int Jp, int64_t ld, int num_sms, int cap, LoopLaunch* L) {
     const int nteams = kk.ncw / kk.tw;
-    const size_t comb = (size_t)((nteams + 1) / 2) * Jp * sizeof(float);
-    const size_t row_bytes = (size_t)ld * sizeof(float);
     const size_t budget = 232448 - 2048;  // 227 KB per block minus static shared memory
-    int rpt = (int)std::max<size_t>(1, 24576 / ((size_t)nteams * row_bytes));
-    bool planned = false;
-    while (!planned) {
-        const int rs = nteams * rpt;
-        const int64_t blocks = (I + rs - 1) / rs;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>({blocks, (int64_t)num_sms, (int64_t)cap}));
-        const int64_t bpc = (blocks + grid - 1) / grid;  // most blocks any CTA owns
-        const int rmax = (int)std::min<int64_t>(bpc * rs, I);
-        const size_t off_G = round_up(SMEM_HDR + comb, 16);
-        const size_t off_F = round_up(off_G + (size_t)Jp * sizeof(float), 16);
-        const size_t off_P = off_F + (size_t)2 * rmax * sizeof(float2);
-        const size_t off_ring = round_up(off_P + (size_t)rmax * sizeof(float), 128);
-        const size_t stage = (size_t)rs * row_bytes;
-        const int stages = off_ring < budget ? (int)std::min<size_t>(MAX_STAGES, (budget - off_ring) / stage) : 0;
-        if (stages >= 3 || (stages >= 2 && rpt == 1)) {
-            L->cfg.rpt = rpt;
-            L->cfg.rows_per_stage = rs;
-            L->cfg.stages = stages;
-            L->cfg.stage_floats = (int)(stage / sizeof(float));
-            L->cfg.rmax = rmax;
-            L->cfg.off_G = (int)off_G;
-            L->cfg.off_F = (int)off_F;
-            L->cfg.off_P = (int)off_P;
-            L->cfg.off_ring = (int)off_ring;
-            L->smem = off_ring + (size_t)stages * stage;
-            L->grid = grid;
-            planned = true;
-        } else if (rpt == 1) {
-            return OT_EUNSUPPORTED;  // the rows a CTA owns do not fit next to two stages
-        } else {
-            rpt = std::max(1, rpt / 2);
-        }
-    }
+    StreamCfg S;
+    size_t smem = 0;
+    int V = 1;
+    // the partitions depend on I and the stage rows only; ask with one CTA per partition
+    if (!plan_stage(nteams, I, Jp, ld, 1, 24576, (size_t)1 << 40, &S, &smem, &V)) return OT_EUNSUPPORTED;
+    const int grid = std::max(1, std::min({V, num_sms, cap}));
+    if (!plan_stage(nteams, I, Jp, ld, grid, 24576, budget, &L->cfg, &L->smem, &L->V))
+        return OT_EUNSUPPORTED;  // the rows a CTA owns do not fit next to two stages
+    L->grid = grid;
     if (cudaFuncSetAttribute(kk.solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem) != cudaSuccess) {
         cudaGetLastError();
         return OT_ECUDA;
@@ -405,16 +213,16 @@ struct SolveBufs {
     DevScalars* sc;
     LoopState* ls;
     SolveSummary* summ;
-    double2* cols;
-    double* G;
-    double* errpart;
-    void* colpart;
-    float2* F;
+    double2* cols;    // [Jp]
+    double* G;        // [3][Jp]
+    double* errpart;  // [2][nb]: loop residual pairs, then the finalize row residuals
+    void* colpart;    // [nb][Jp] float2
+    double2* fpart;   // [nb][Jp]
 };
 
 // Enqueue the whole solve; the caller copies B.summ back.
-cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunch& LL, int nb_fin, size_t smem_fin,
-                          const SolveBufs& B, long long spin, cudaStream_t s, ot_assoc_ctx* ctx) {
+cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunch& LL, const SolveBufs& B,
+                          long long spin, cudaStream_t s, ot_assoc_ctx* ctx) {
     const int J = a.J;
     const int64_t I = a.I;
     const int Jp = (int)round_up(J, 4);
@@ -430,6 +238,7 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
     P.I = I;
     P.J = J;
     P.Jp = Jp;
+    P.V = LL.V;
     P.p = a.p;
     P.q = a.q;
     P.g_warm = a.warm_start ? a.out->g : nullptr;
@@ -437,7 +246,7 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
     P.sc = B.sc;
     P.st = B.ls;
     P.G = B.G;
-    P.F_out = B.F;
+    P.F_out = nullptr;
     P.colpart = (float*)B.colpart;
     P.errpart = B.errpart;
     P.k = k;
@@ -446,6 +255,12 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
     P.tol = a.tol;
     P.max_iter = a.max_iter;
     P.spin = spin;
+    P.fpart = B.fpart;
+    P.epart = B.errpart + LL.V;
+    P.pi = a.out->pi;
+    P.pi_ld = a.out->pi_ld > 0 ? a.out->pi_ld : J;
+    P.f_nat = a.out->f;
+    P.eps_ln2 = a.eps * LN2;
     if (ctx) timing_mark(ctx, 1, s);
     {
         void* args[] = {&P, (void*)&LL.cfg};
@@ -453,34 +268,10 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
         if (e != cudaSuccess) return e;
     }
     if (ctx) timing_mark(ctx, 2, s);
-    FinParams Q;
-    Q.C = a.C;
-    Q.ld = a.ld;
-    Q.I = I;
-    Q.J = J;
-    Q.Jp = Jp;
-    Q.p = a.p;
-    Q.sc = B.sc;
-    Q.st = B.ls;
-    Q.F = B.F;
-    Q.G = B.G;
-    Q.k_hi = k_hi;
-    Q.k_lo = k_lo;
-    Q.eps_ln2 = a.eps * LN2;
-    Q.pi = a.out->pi;
-    Q.pi_ld = a.out->pi_ld > 0 ? a.out->pi_ld : J;
-    Q.f_out = a.out->f;
-    Q.fpart = (double2*)B.colpart;
-    Q.epart = B.errpart;
-    {
-        void* args[] = {&Q};
-        e = cudaLaunchKernel(kk.fin, dim3(nb_fin), dim3(NT_F), args, smem_fin, s);
-        if (e != cudaSuccess) return e;
-    }
-    const int nb_cols = (int)std::max<int64_t>((J + 15) / 16, std::min<int64_t>((I + 511) / 512, 1024));
-    sk_finalize_cols<<<nb_cols, 512, 0, s>>>((const double2*)B.colpart, nb_fin, Jp, J, a.q, B.sc, B.ls, B.G,
-                                             a.eps * LN2, a.out->g, a.out->rrh_load, B.cols, B.F, a.p, I, a.out->f);
-    sk_summary<<<1, 256, 0, s>>>(B.errpart, nb_fin, B.cols, J, B.sc, B.ls, B.summ);
+    const int nb_cols = (int)std::max<int64_t>(1, std::min<int64_t>((J + 15) / 16, 1024));
+    sk_finalize_cols<<<nb_cols, 512, 0, s>>>(B.fpart, LL.V, Jp, J, a.q, B.sc, B.ls, B.G, a.eps * LN2, a.out->g,
+                                             a.out->rrh_load, B.cols);
+    sk_summary<<<1, 256, 0, s>>>(P.epart, LL.V, B.cols, J, B.sc, B.ls, B.summ);
     if (ctx) timing_mark(ctx, 3, s);
     return cudaGetLastError();
 }
@@ -497,19 +288,14 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
     LoopLaunch LL;
     st = plan_solve(kk, I, Jp, a.ld, ctx->num_sms, 1 << 30, &LL);
     if (st) return set_error(ctx, st, "solver does not fit the shared memory (I=%lld J=%d)", (long long)I, J);
-    int nb_fin = 1;
-    size_t smem_fin = 0;
-    st = plan_finalize(kk, I, Jp, ctx->num_sms, 1 << 30, &nb_fin, &smem_fin);
-    if (st) return set_error(ctx, st, "finalize launch setup failed");
-    const int nb_part = std::max(LL.grid, nb_fin);
     SolveBufs B;
-    B.F = (float2*)scratch(ctx, SLOT_F, sizeof(float2) * (size_t)I, &st);
+    B.colpart = scratch(ctx, SLOT_COLPART, sizeof(float2) * (size_t)LL.V * Jp, &st);
+    if (st) return st;
+    B.fpart = (double2*)scratch(ctx, SLOT_FINPART, sizeof(double2) * (size_t)LL.V * Jp, &st);
     if (st) return st;
     B.G = (double*)scratch(ctx, SLOT_G, sizeof(double) * 3 * (size_t)Jp, &st);
     if (st) return st;
-    B.colpart = scratch(ctx, SLOT_COLPART, sizeof(double2) * (size_t)nb_part * Jp, &st);
-    if (st) return st;
-    B.errpart = (double*)scratch(ctx, SLOT_ERRPART, sizeof(double) * 2 * (size_t)nb_part, &st);
+    B.errpart = (double*)scratch(ctx, SLOT_ERRPART, sizeof(double) * 2 * (size_t)LL.V, &st);
     if (st) return st;
     char* state = (char*)scratch(ctx, SLOT_STATE, 4096 + sizeof(double2) * (size_t)Jp, &st);
     if (st) return st;
@@ -521,9 +307,9 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
     if (st) return st;
     ctx->last_timings.valid = 0;
     cudaStream_t s = a.stream;
-    cudaError_t e = enqueue_solve(a, kk, LL, nb_fin, smem_fin, B, ctx->spin_limit, s, ctx);
+    cudaError_t e = enqueue_solve(a, kk, LL, B, ctx->spin_limit, s, ctx);
     if (e != cudaSuccess) return cuda_error(ctx, e, "solve launch");
-    ctx->launches += 4;
+    ctx->launches += 3;
     e = cudaMemcpyAsync(hsum, B.summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_error(ctx, e, "summary copy");
     e = cudaStreamSynchronize(s);
@@ -546,7 +332,7 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
 static constexpr size_t NOALLOC_BYTES = size_t(8) << 20;  // 8 MiB
 static constexpr int64_t NOALLOC_MAX_I = 131072;
 static constexpr int NOALLOC_MAX_J = 1024;
-static constexpr int NOALLOC_MAX_CTAS = 320;
+static constexpr int NOALLOC_MAX_CTAS = 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
@@ -555,11 +341,11 @@ static constexpr size_t NA_STATE = 0;                                     // Dev
 static constexpr size_t NA_COLS = 4096;                                   // Jp double2
 static constexpr size_t NA_G = NA_COLS + 16 * NOALLOC_MAX_J;              // 3 * Jp doubles
 static constexpr size_t NA_ERRPART = NA_G + 24 * NOALLOC_MAX_J;           // 2 * CTAs doubles
-static constexpr size_t NA_COLPART = NA_ERRPART + 16 * NOALLOC_MAX_CTAS;  // CTAs * Jp double2
-static constexpr size_t NA_F = NA_COLPART + 16 * (size_t)NOALLOC_MAX_CTAS * NOALLOC_MAX_J;
-static constexpr size_t NA_END = NA_F + 16 * (size_t)NOALLOC_MAX_I;       // I float2 (+ room)
+static constexpr size_t NA_COLPART = NA_ERRPART + 16 * NOALLOC_MAX_CTAS;  // CTAs * Jp float2
+static constexpr size_t NA_FPART = NA_COLPART + 8 * (size_t)NOALLOC_MAX_CTAS * NOALLOC_MAX_J;  // CTAs * Jp double2
+static constexpr size_t NA_END = NA_FPART + 16 * (size_t)NOALLOC_MAX_CTAS * NOALLOC_MAX_J;
 static_assert(NA_END <= NOALLOC_BYTES, "no-allocation scratch layout does not fit");
-static_assert(NA_COLPART % 256 == 0 && NA_F % 256 == 0, "alignment");
+static_assert(NA_COLPART % 256 == 0 && NA_FPART % 256 == 0, "alignment");
 
 // Device address of g_noalloc_scratch per device, looked up once with that device current.
 static std::mutex g_noalloc_mu;
@@ -599,10 +385,6 @@ static ot_status noalloc_solve(const SolveArgs& a, SolveSummary* sum_host) {
     LoopLaunch LL;
     st = plan_solve(kk, I, Jp, a.ld, nsm, NOALLOC_MAX_CTAS, &LL);
     if (st) return st;
-    int nb_fin = 1;
-    size_t smem_fin = 0;
-    st = plan_finalize(kk, I, Jp, nsm, NOALLOC_MAX_CTAS, &nb_fin, &smem_fin);
-    if (st) return st;
     SolveBufs B;
     char* state = (char*)(base + NA_STATE);
     B.sc = (DevScalars*)state;
@@ -612,10 +394,10 @@ static ot_status noalloc_solve(const SolveArgs& a, SolveSummary* sum_host) {
     B.G = (double*)(base + NA_G);
     B.errpart = (double*)(base + NA_ERRPART);
     B.colpart = (void*)(base + NA_COLPART);
-    B.F = (float2*)(base + NA_F);
+    B.fpart = (double2*)(base + NA_FPART);
     // The state words are cleared at the start of every call (the array keeps the last
     // call's data); enqueue_solve does that first.
-    cudaError_t e = enqueue_solve(a, kk, LL, nb_fin, smem_fin, B, 1LL << 24, a.stream, nullptr);
+    cudaError_t e = enqueue_solve(a, kk, LL, B, 1LL << 24, a.stream, nullptr);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sum_host, B.summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, a.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(a.stream);
     if (e != cudaSuccess) {

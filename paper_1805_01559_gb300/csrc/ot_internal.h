@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "ot_assoc.h"
 
@@ -30,7 +31,8 @@ enum ScratchSlot {
     SLOT_COUNT
 };
 
-// Batched solver tuning: one entry per size bucket (cells class x J class).
+// Batched solver tuning: group size (schedule) and stage size (tile) per instance size
+// bucket (cells class x J class).
 static constexpr int TUNE_BUCKETS = 15;
 struct TuneEntry {
     int gsize = 0;   // CTAs per instance group (0 = not tuned: use the default)

@@ -204,6 +204,7 @@ struct SolveParams {
     int64_t I;
     int J;
     int Jp;
+    int V;            // row partitions (see part_row): the unit of every cross-row reduction
     const float* p;
     const float* q;
     const double* g_warm;                 // warm-start g (natural units) or nullptr
@@ -212,21 +213,97 @@ struct SolveParams {
     LoopState* st;
     double* G;        // [3][Jp]: column potentials G^k (log2 units, FP64) in buffer k & 1,
                       // then log2 q^_j (set once per solve)
-    float2* F_out;    // [I] row potentials of the returned plan (hi, lo)
-    float* colpart;   // [nb][2 * Jp]
-    double* errpart;  // [nb] during setup (sums of p); reused as float2 [nb] residual pairs
+    float2* F_out;    // [I] row potentials of the returned plan (hi, lo), or nullptr
+    float* colpart;   // [V][2 * Jp]
+    double* errpart;  // [V] during setup (sums of p); reused as float2 [V] residual pairs
     double k;
     float k_hi, k_lo;
     double tol;
     int max_iter;
     long long spin;
+    // Finalize sweep after the stop (skipped when fpart is null): column partials
+    // (sum_i p^_i t_ij, sum_i p^_i C_ij t_ij) per partition in FP64, row residual per
+    // partition, and optionally the plan pi_ij = p_i t_ij and the natural-unit row potentials.
+    double2* fpart;   // [V][Jp]
+    double* epart;    // [V]
+    float* pi;        // [I][pi_ld] or nullptr
+    int64_t pi_ld;
+    double* f_nat;    // [I] f_i = eps ln2 (F'_i + log2 p_i), or nullptr
+    double eps_ln2;
 };
 
-// Block-aligned row range of CTA b.
-__device__ __forceinline__ void cta_rows(int64_t I, int rs, int b, int nb, int64_t* r0, int64_t* r1) {
+// Row partitions.  The I rows form B = ceil(I / rs) stage blocks of rs rows; partition v of V
+// is the run of blocks [B v / V, B (v + 1) / V).  Every sum over rows (column partials, row
+// residuals, sums of p) is formed per partition, in a fixed order inside it, and partitions
+// are combined in partition order, so the result does not depend on how many CTAs share the
+// work: a CTA owns a contiguous run of partitions and walks them one after the other.
+__host__ __device__ __forceinline__ int64_t part_row(int64_t I, int rs, int V, int v) {
     const int64_t B = (I + rs - 1) / rs;
-    *r0 = (B * b / nb) * rs;
-    *r1 = min(I, (B * (b + 1) / nb) * (int64_t)rs);
+    const int64_t r = (B * v / V) * rs;
+    return r < I ? r : I;
+}
+__host__ __device__ __forceinline__ void cta_parts(int V, int b, int nb, int* v0, int* v1) {
+    *v0 = (int)((int64_t)V * b / nb);
+    *v1 = (int)((int64_t)V * (b + 1) / nb);
+}
+// Rows [r0, r1) of CTA b of nb.
+__host__ __device__ __forceinline__ void cta_rows(int64_t I, int rs, int V, int b, int nb, int64_t* r0,
+                                                  int64_t* r1) {
+    int v0, v1;
+    cta_parts(V, b, nb, &v0, &v1);
+    *r0 = part_row(I, rs, V, v0);
+    *r1 = part_row(I, rs, V, v1);
+}
+// Partitions of an instance: at most VMAX, at least one stage block and 64 rows each.
+static constexpr int VMAX = 152;
+__host__ __device__ __forceinline__ int parts_for(int64_t I, int rs) {
+    const int64_t B = (I + rs - 1) / rs;
+    int64_t v = I / 64;
+    if (v > B) v = B;
+    if (v > VMAX) v = VMAX;
+    return v < 1 ? 1 : (int)v;
+}
+
+// Stage geometry and shared-memory layout of an instance solved by nb CTAs with teams of
+// `nteams` rows.  The rows per stage depend only on the stage target and the row length,
+// and the partitions only on I and the rows per stage: the arithmetic of a solve is fixed
+// by (I, J, ld, stage target) whatever nb is.  Returns false when a CTA's rows do not fit
+// next to two stages.
+inline bool plan_stage(int nteams, int64_t I, int Jp, int64_t ld, int nb, int stage_target, size_t budget,
+                       StreamCfg* S, size_t* smem, int* Vout) {
+    const size_t comb = (size_t)((nteams + 1) / 2) * Jp * sizeof(float);
+    const size_t row_bytes = (size_t)ld * sizeof(float);
+    const int rpt = (int)(stage_target / ((size_t)nteams * row_bytes) > 1 ? stage_target / ((size_t)nteams * row_bytes)
+                                                                           : 1);
+    const int rs = nteams * rpt;
+    const int V = parts_for(I, rs);
+    int64_t rmax = 0;
+    for (int b = 0; b < nb; ++b) {
+        int64_t r0, r1;
+        cta_rows(I, rs, V, b, nb, &r0, &r1);
+        rmax = r1 - r0 > rmax ? r1 - r0 : rmax;
+    }
+    auto up = [](size_t x, size_t m) { return (x + m - 1) / m * m; };
+    const size_t off_G = up(SMEM_HDR + comb, 16);
+    const size_t off_F = up(off_G + (size_t)Jp * sizeof(float), 16);
+    const size_t off_P = off_F + (size_t)2 * rmax * sizeof(float2);
+    const size_t off_ring = up(off_P + (size_t)rmax * sizeof(float), 128);
+    const size_t stage = (size_t)rs * row_bytes;
+    const size_t room = off_ring < budget ? (budget - off_ring) / stage : 0;
+    const int stages = (int)(room < (size_t)MAX_STAGES ? room : (size_t)MAX_STAGES);
+    if (stages < 2) return false;
+    S->rpt = rpt;
+    S->rows_per_stage = rs;
+    S->stages = stages;
+    S->stage_floats = (int)(stage / sizeof(float));
+    S->rmax = (int)(rmax > 0 ? rmax : 1);
+    S->off_G = (int)off_G;
+    S->off_F = (int)off_F;
+    S->off_P = (int)off_P;
+    S->off_ring = (int)off_ring;
+    *smem = off_ring + (size_t)stages * stage;
+    *Vout = V;
+    return true;
 }
 
 // Sum of (s, e) pairs over a warp with error-free additions.
@@ -244,11 +321,12 @@ __device__ __forceinline__ void warp_sum_pair(float& s, float& e) {
 
 // Shared-memory words of the consumer warps (and the producer's stop flag).
 struct SkShared {
-    float red[32];          // team reductions: 2 * NTEAMS * TW <= 24
+    float red[64];          // team reductions: 2 * NTEAMS * TW <= 24 values (float2 pairs: 48 floats)
     float errf[12];         // per-team row residuals
     double sh_sum[12][2];   // per-warp setup sums
     int s_dec, s_ok, s_bad;
     volatile int s_stop;    // consumers -> producer: stop streaming
+    int pend[VMAX + 1];     // stage blocks (from the CTA's first row) at which its partitions end
 };
 
 // The CTAs that solve one instance together: nb CTAs, this one is number b.  `bar` counts
@@ -263,9 +341,178 @@ struct GroupCtx {
     int* status;
 };
 
-// The consumer warps' part of one solve (Algorithm 1 on the CTA's rows [r0, r1)): setup,
-// the exact first sweep, then plan-scale sweeps until the loop test stops.  Returns true
-// when the loop stopped normally (the returned plan's row potentials are then in row
+// Team sum of per-lane FP32 values as an error-free (hi, lo) pair; `red` holds 4 * NTEAMS * TW
+// floats, the halves alternating by `par` as in team_reduce.
+template <int TW>
+__device__ __forceinline__ float2 team_sum_pair(float s, float* red, int nteams, const Team<TW>& tm, int& par) {
+    float e = 0.f;
+    warp_sum_pair(s, e);
+    if constexpr (TW == 1) {
+        return make_float2(s, e);
+    } else {
+        float2* r = reinterpret_cast<float2*>(red) + (par * nteams + tm.team) * TW;
+        if (tm.lane == 0) r[tm.wit] = make_float2(s, e);
+        bar_named(1 + tm.team, 32 * TW);
+        float2 a = r[0];
+#pragma unroll
+        for (int w = 1; w < TW; ++w) a = df_add2(a, r[w]);
+        par ^= 1;
+        return a;
+    }
+}
+
+// Sum of the teams' float4 column partials acc (in team order: the first half of the teams
+// stores, the second half adds onto slot team - HALF, then the HALF slots are summed in
+// order); f(j, sum) receives column j's total.  Named barriers over the consumer warps; the
+// comb buffer (HALF rows of Jp floats) is free again when it returns.
+template <int TW, int VPT, typename Fn>
+__device__ __forceinline__ void cta_col_sum(float* comb, const float4 (&acc)[VPT], int J, int Jp, const Team<TW>& tm,
+                                            Fn f) {
+    constexpr int NCW = Cons<TW>::NCW;
+    constexpr int TT = 32 * TW, NTEAMS = NCW / TW, NC = NCW * 32;
+    constexpr int HALF = (NTEAMS + 1) / 2;
+    if (tm.team < HALF) {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int col = 4 * (tm.tl + TT * v);
+            if (col < Jp) *reinterpret_cast<float4*>(comb + tm.team * Jp + col) = acc[v];
+        }
+    }
+    bar_named(CONS_BAR, NC);
+    if (tm.team >= HALF) {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int col = 4 * (tm.tl + TT * v);
+            if (col < Jp) {
+                float4* d = reinterpret_cast<float4*>(comb + (tm.team - HALF) * Jp + col);
+                float4 o = *d;
+                o.x += acc[v].x;
+                o.y += acc[v].y;
+                o.z += acc[v].z;
+                o.w += acc[v].w;
+                *d = o;
+            }
+        }
+    }
+    bar_named(CONS_BAR, NC);
+    for (int j = threadIdx.x; j < J; j += NC) {
+        float sum = comb[j];
+        for (int t = 1; t < HALF; ++t) sum += comb[t * Jp + j];
+        f(j, sum);
+    }
+    bar_named(CONS_BAR, NC);
+}
+
+// Finalize sweep of the consumer warps, run right after the loop stops: the producer has
+// already streamed the next pass over the CTA's rows into the ring, so this is one more
+// sweep at streaming speed.  Plan of the returned potentials F' (Fold) and G (Gs, still the
+// returned plan's column potentials): t_ij = 2^(F'_i + G_j - k C_ij).  Each team keeps FP32
+// column sums of p^ t and p^ C t over at most FIN_ROWS rows, then the CTA adds the teams'
+// sums (in team order) into the partition's FP64 partials P.fpart[v]; the row residual
+// sum_i p^_i |sum_j t_ij - 1| uses error-free row sums.
+static constexpr int FIN_ROWS = 16;
+template <int TW, int VPT>
+__device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const StreamCfg& S, SkShared* sh,
+                                                  unsigned char* dyn, int64_t r0, int nrow, int v0, int v1,
+                                                  const float2* Fold, uint32_t& cseq, int* abort) {
+    constexpr int NCW = Cons<TW>::NCW;
+    constexpr int TT = 32 * TW, NTEAMS = NCW / TW, NC = NCW * 32;
+    uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
+    uint64_t* empty = full + MAX_STAGES;
+    float* comb = reinterpret_cast<float*>(dyn + SMEM_HDR);
+    const float* Gs = reinterpret_cast<const float*>(dyn + S.off_G);
+    const float* Ps = reinterpret_cast<const float*>(dyn + S.off_P);
+    const float* ring = reinterpret_cast<const float*>(dyn + S.off_ring);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int J = P.J, Jp = P.Jp, rs_ = S.rows_per_stage;
+    const Team<TW> tm;
+    int par = 0;
+    for (int v = v0; v < v1; ++v)
+        for (int j = tid; j < J; j += NC) P.fpart[(int64_t)v * Jp + j] = make_double2(0.0, 0.0);
+    float4 cpi[VPT], crho[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) cpi[v] = crho[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float errt = 0.f;
+    const int nblk = (nrow + rs_ - 1) / rs_;
+    const int every = max(1, FIN_ROWS / S.rpt);  // stages between flushes
+    const int* pend = sh->pend - v0;
+    int vp = v0, vbeg = 0;
+    int vend = v0 < v1 ? pend[v0] : 0;
+    for (int kb = 0; kb < nblk; ++kb) {
+        const int st = (int)(cseq % (uint32_t)S.stages);
+        const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
+        const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, abort);
+        const int lr0 = kb * rs_;
+        const int rows = min(rs_, nrow - lr0);
+        const float* stage = ring + (size_t)st * S.stage_floats;
+        for (int jr = 0; ok && jr < S.rpt; ++jr) {
+            const int rr = tm.team + NTEAMS * jr;
+            if (rr >= rows) break;
+            const int lr = lr0 + rr;
+            const float* row = stage + (size_t)rr * P.ld;
+            const float2 F = Fold[lr];
+            const float phat = Ps[lr];
+            const int64_t i = r0 + lr;
+            const float pf = P.pi ? __ldg(P.p + i) : 0.f;
+            float rsum = 0.f;
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int col = 4 * (tm.tl + TT * v);
+                if (chunk_inside<TW, VPT>(v) || col < J) {
+                    float4 x = *reinterpret_cast<const float4*>(row + col);
+                    float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float cost = comp(x, c);
+                        float t = ex2(expo(F.x, F.y + comp(gv, c), cost, P.k_hi, P.k_lo));
+                        if (!chunk_inside<TW, VPT>(v) && col + c >= J) t = 0.f;  // past the row
+                        rsum += t;
+                        comp(cpi[v], c) = fmaf(phat, t, comp(cpi[v], c));
+                        comp(crho[v], c) = fmaf(phat, t > 0.f ? cost * t : 0.f, comp(crho[v], c));
+                        if (P.pi && col + c < J) P.pi[i * P.pi_ld + col + c] = pf * t;
+                    }
+                }
+            }
+            const float2 r = team_sum_pair<TW>(rsum, sh->red, NTEAMS, tm, par);
+            errt = fmaf(phat, fabsf((r.x - 1.0f) + r.y), errt);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        ++cseq;
+        const bool at_end = (kb + 1 == vend);
+        if ((kb + 1 - vbeg) % every == 0 || at_end) {
+            double2* fp = P.fpart + (int64_t)vp * Jp;
+            cta_col_sum<TW, VPT>(comb, cpi, J, Jp, tm, [&](int j, float sum) { fp[j].x += (double)sum; });
+            cta_col_sum<TW, VPT>(comb, crho, J, Jp, tm, [&](int j, float sum) { fp[j].y += (double)sum; });
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) cpi[v] = crho[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (at_end) {
+            if (tm.tl == 0) sh->errf[tm.team] = errt;
+            bar_named(CONS_BAR, NC);
+            if (tid == 0) {
+                float2 e = make_float2(sh->errf[0], 0.f);
+                for (int t = 1; t < NTEAMS; ++t) e = df_add(e, sh->errf[t]);
+                P.epart[vp] = (double)e.x + (double)e.y;
+            }
+            bar_named(CONS_BAR, NC);
+            errt = 0.f;
+            ++vp;
+            vbeg = kb + 1;
+            if (vp < v1) vend = pend[vp];
+        }
+    }
+    // natural-unit row potentials, one row per thread (an FP64 log2 each, off the sweep)
+    if (P.f_nat)
+        for (int r = tid; r < nrow; r += NC) {
+            const float2 F = Fold[r];
+            P.f_nat[r0 + r] = P.eps_ln2 * ((double)F.x + (double)F.y + log2((double)__ldg(P.p + r0 + r)));
+        }
+}
+
+// The consumer warps' part of one solve (Algorithm 1 on the CTA's partitions, rows [r0, r1)):
+// setup, the exact first sweep, then plan-scale sweeps until the loop test stops.  Returns
+// true when the loop stopped normally (the returned plan's row potentials are then in row
 // potential buffer *ret_par of shared memory, and in P.F_out when given), false when the
 // instance failed or a wait gave up.  Either way s_stop is raised for the producer.
 // Every decision that ends the loop is taken identically by every CTA of the group.
@@ -274,7 +521,8 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                                              unsigned char* dyn, int64_t r0, int64_t r1, int* ret_par) {
     constexpr int NCW = Cons<TW>::NCW;
     constexpr int TT = 32 * TW, NTEAMS = NCW / TW, NC = NCW * 32;
-    static_assert(2 * NTEAMS * TW <= 32 && NTEAMS <= 12 && NCW <= 12, "SkShared sizes");
+    constexpr int HALF = (NTEAMS + 1) / 2;
+    static_assert(4 * NTEAMS * TW <= 64 && NTEAMS <= 12 && NCW <= 12, "SkShared sizes");
     uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
     uint64_t* empty = full + MAX_STAGES;
     float* comb = reinterpret_cast<float*>(dyn + SMEM_HDR);    // [ceil(NTEAMS / 2)][Jp]
@@ -290,10 +538,16 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
     volatile int& s_stop = sh->s_stop;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = g.nb, b = g.b;
+    const int V = P.V, rs_ = S.rows_per_stage;
+    int v0, v1;
+    cta_parts(V, b, nb, &v0, &v1);
     const int nrow = (int)max((int64_t)0, r1 - r0);
     int* status = g.status;
     const int J = P.J, Jp = P.Jp;
     const int tid = threadIdx.x;
+    // stage blocks (from the CTA's first row) at which each of the CTA's partitions ends
+    for (int v = v0 + tid; v < v1; v += NC) sh->pend[v - v0] = (int)((part_row(P.I, rs_, V, v + 1) - r0 + rs_ - 1) / rs_);
+    const int* pend = sh->pend - v0;
 #define OTA_BARRIER()                                                                              \
     do {                                                                                           \
         if (!grid_barrier_named(g.bar, (unsigned)nb * ++g.gen, g.abort, P.spin, CONS_BAR, NC, &sh->s_ok)) { \
@@ -313,15 +567,27 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
         }                                                                                          \
     } while (0)
 
-    // ---- setup: sums of p (per CTA) and q (every CTA), checks, starting G ----------------
+    // ---- setup: sums of p (per partition) and q (every CTA), checks, starting G ----------
     {
-        double sp = 0.0;
         int bad = 0;
-        for (int r = tid; r < nrow; r += NC) {
-            const float v = __ldg(P.p + r0 + r);
-            bad |= !(v > 0.0f) || !isfinite(v);
-            sp += (double)v;
-            Ps[r] = v;
+        for (int v = v0; v < v1; ++v) {
+            const int a = (int)(part_row(P.I, rs_, V, v) - r0), e = (int)(part_row(P.I, rs_, V, v + 1) - r0);
+            double sp = 0.0;
+            for (int r = a + tid; r < e; r += NC) {
+                const float x = __ldg(P.p + r0 + r);
+                bad |= !(x > 0.0f) || !isfinite(x);
+                sp += (double)x;
+                Ps[r] = x;
+            }
+            sp = warp_sum(sp);
+            if (lane == 0) sh_sum[warp][0] = sp;
+            bar_named(CONS_BAR, NC);
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < NCW; ++w) t += sh_sum[w][0];
+                P.errpart[v] = t;
+            }
+            bar_named(CONS_BAR, NC);
         }
         const int gw = b * NCW + warp, nw = nb * NCW;
         for (int j = gw * 32 + lane; j < J; j += nw * 32) {
@@ -330,16 +596,9 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             P.G[j] = g0;
         }
         if (b == 0 && tid == 0 && P.input_bad && *P.input_bad) bad = 1;
-        sp = warp_sum(sp);
-        if (lane == 0) sh_sum[warp][0] = sp;
         if (bad) atomicOr(&s_bad, 1);
         bar_named(CONS_BAR, NC);
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < NCW; ++w) t += sh_sum[w][0];
-            P.errpart[b] = t;
-            if (s_bad) atomicCAS(status, DEV_OK, DEV_EINVAL);
-        }
+        if (tid == 0 && s_bad) atomicCAS(status, DEV_OK, DEV_EINVAL);
     }
     OTA_BARRIER_CHECK();
     double sp = 0.0, sq = 0.0;
@@ -347,11 +606,11 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
         // every CTA forms the same totals in the same order
         double a = 0.0, c = 0.0;
         int badq = 0;
-        for (int bb = tid; bb < nb; bb += NC) a += P.errpart[bb];
+        for (int bb = tid; bb < V; bb += NC) a += P.errpart[bb];
         for (int j = tid; j < J; j += NC) {
-            const float v = __ldg(P.q + j);
-            badq |= !(v > 0.0f) || !isfinite(v);
-            c += (double)v;
+            const float x = __ldg(P.q + j);
+            badq |= !(x > 0.0f) || !isfinite(x);
+            c += (double)x;
         }
         a = warp_sum(a);
         c = warp_sum(c);
@@ -391,7 +650,6 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
         bar_named(CONS_BAR, NC);
     }
     const Team<TW> tm;
-    const int nblk = (nrow + S.rows_per_stage - 1) / S.rows_per_stage;
     load_G_smem(P.G, J, Jp, Gs, tid, NC);
     bar_named(CONS_BAR, NC);
     uint32_t cseq = 0;
@@ -406,12 +664,16 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             Sm[v] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float2* F1 = Fs + S.rmax;  // F'^1 lives in buffer 1
-        for (int kb = 0; kb < nblk; ++kb) {
+        float2* part2 = reinterpret_cast<float2*>(P.colpart);
+        int kb = 0;
+        for (int vp = v0; vp < v1; ++vp) {
+          const int vend = pend[vp];
+          for (; kb < vend; ++kb) {
             const int st = (int)(cseq % (uint32_t)S.stages);
             const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
             const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, g.abort);
-            const int lr0 = kb * S.rows_per_stage;
-            const int rows = min(S.rows_per_stage, nrow - lr0);
+            const int lr0 = kb * rs_;
+            const int rows = min(rs_, nrow - lr0);
             const float* stage = ring + (size_t)st * S.stage_floats;
             for (int j = 0; ok && j < S.rpt; ++j) {
                 const int rr = tm.team + NTEAMS * j;
@@ -467,74 +729,81 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
             ++cseq;
-        }
-        // CTA merge of the (max, sum) pairs in two rounds through the float buffer: the column
-        // maxima first (kept in Gs, which is reloaded after the next grid barrier anyway),
-        // then the sums rescaled to them; teams in a fixed order.
-        constexpr int HALF = (NTEAMS + 1) / 2;
-        for (int round = 0; round < 2; ++round) {  // the first half stores, the second half merges
-            if ((tm.team < HALF) == (round == 0)) {
-                const int slot = round == 0 ? tm.team : tm.team - HALF;
+          }
+            // end of partition vp: merge the teams' (max, sum) pairs in two rounds through
+            // the float buffer, the column maxima first (held in Gs meanwhile), then the sums
+            // rescaled to them; teams in a fixed order.  Gs gets G^0 back afterwards.
+            for (int round = 0; round < 2; ++round) {  // the first half stores, the second half merges
+                if ((tm.team < HALF) == (round == 0)) {
+                    const int slot = round == 0 ? tm.team : tm.team - HALF;
 #pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    const int col = 4 * (tm.tl + TT * v);
-                    if (col < Jp) {
-                        float4* d = reinterpret_cast<float4*>(comb + slot * Jp + col);
-                        if (round == 0) {
-                            *d = M[v];
-                        } else {
-                            float4 o = *d;
-                            o.x = fmaxf(o.x, M[v].x);
-                            o.y = fmaxf(o.y, M[v].y);
-                            o.z = fmaxf(o.z, M[v].z);
-                            o.w = fmaxf(o.w, M[v].w);
-                            *d = o;
+                    for (int v = 0; v < VPT; ++v) {
+                        const int col = 4 * (tm.tl + TT * v);
+                        if (col < Jp) {
+                            float4* d = reinterpret_cast<float4*>(comb + slot * Jp + col);
+                            if (round == 0) {
+                                *d = M[v];
+                            } else {
+                                float4 o = *d;
+                                o.x = fmaxf(o.x, M[v].x);
+                                o.y = fmaxf(o.y, M[v].y);
+                                o.z = fmaxf(o.z, M[v].z);
+                                o.w = fmaxf(o.w, M[v].w);
+                                *d = o;
+                            }
                         }
                     }
                 }
+                bar_named(CONS_BAR, NC);
+            }
+            for (int j = tid; j < Jp; j += NC) {
+                float mm = comb[j];
+                for (int t = 1; t < HALF; ++t) mm = fmaxf(mm, comb[t * Jp + j]);
+                Gs[j] = mm;
             }
             bar_named(CONS_BAR, NC);
-        }
-        for (int j = tid; j < Jp; j += NC) {
-            float mm = comb[j];
-            for (int t = 1; t < HALF; ++t) mm = fmaxf(mm, comb[t * Jp + j]);
-            Gs[j] = mm;
-        }
-        bar_named(CONS_BAR, NC);
-        for (int round = 0; round < 2; ++round) {
-            if ((tm.team < HALF) == (round == 0)) {
-                const int slot = round == 0 ? tm.team : tm.team - HALF;
+            for (int round = 0; round < 2; ++round) {
+                if ((tm.team < HALF) == (round == 0)) {
+                    const int slot = round == 0 ? tm.team : tm.team - HALF;
 #pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    const int col = 4 * (tm.tl + TT * v);
-                    if (col < Jp) {
-                        float4 sc;
+                    for (int v = 0; v < VPT; ++v) {
+                        const int col = 4 * (tm.tl + TT * v);
+                        if (col < Jp) {
+                            float4 sc;
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const float Mc = comp(M[v], c), mm = Gs[col + c];
-                            comp(sc, c) = Mc > -INFINITY ? comp(Sm[v], c) * ex2(Mc - mm) : 0.f;
-                        }
-                        float4* d = reinterpret_cast<float4*>(comb + slot * Jp + col);
-                        if (round == 0) {
-                            *d = sc;
-                        } else {
-                            float4 o = *d;
-                            o.x += sc.x;
-                            o.y += sc.y;
-                            o.z += sc.z;
-                            o.w += sc.w;
-                            *d = o;
+                            for (int c = 0; c < 4; ++c) {
+                                const float Mc = comp(M[v], c), mm = Gs[col + c];
+                                comp(sc, c) = Mc > -INFINITY ? comp(Sm[v], c) * ex2(Mc - mm) : 0.f;
+                            }
+                            float4* d = reinterpret_cast<float4*>(comb + slot * Jp + col);
+                            if (round == 0) {
+                                *d = sc;
+                            } else {
+                                float4 o = *d;
+                                o.x += sc.x;
+                                o.y += sc.y;
+                                o.z += sc.z;
+                                o.w += sc.w;
+                                *d = o;
+                            }
                         }
                     }
                 }
+                bar_named(CONS_BAR, NC);
+            }
+            for (int j = tid; j < J; j += NC) {
+                float ss = comb[j];
+                for (int t = 1; t < HALF; ++t) ss += comb[t * Jp + j];
+                part2[(int64_t)vp * Jp + j] = make_float2(Gs[j], ss);
             }
             bar_named(CONS_BAR, NC);
-        }
-        float2* part2 = reinterpret_cast<float2*>(P.colpart);
-        for (int j = tid; j < J; j += NC) {
-            float ss = comb[j];
-            for (int t = 1; t < HALF; ++t) ss += comb[t * Jp + j];
-            part2[(int64_t)b * Jp + j] = make_float2(Gs[j], ss);
+            load_G_smem(P.G, J, Jp, Gs, tid, NC);
+            bar_named(CONS_BAR, NC);
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                M[v] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+                Sm[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
         OTA_BARRIER();
         // G^1_j = G^0_j + log2 q^_j - log2(column sum of pi^(1/2)), one warp per column
@@ -542,11 +811,11 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             const int gw = b * NCW + warp, nw = nb * NCW;
             for (int j = gw; j < J; j += nw) {
                 float mm = -INFINITY;
-                for (int bb = lane; bb < nb; bb += 32) mm = fmaxf(mm, part2[(int64_t)bb * Jp + j].x);
+                for (int bb = lane; bb < V; bb += 32) mm = fmaxf(mm, part2[(int64_t)bb * Jp + j].x);
                 mm = warp_max(mm);
                 double ss = 0.0;
                 if (mm > -INFINITY)
-                    for (int bb = lane; bb < nb; bb += 32) {
+                    for (int bb = lane; bb < V; bb += 32) {
                         const float2 o = part2[(int64_t)bb * Jp + j];
                         if (o.x > -INFINITY) ss += (double)o.y * (double)ex2(o.x - mm);
                     }
@@ -567,6 +836,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
     }
 
     // ---- sweeps 2, 3, ...: one read of C and one ex2 per cell -----------------------------
+    float2* errp = reinterpret_cast<float2*>(P.errpart);
     for (int s = 2;; ++s) {
         const float2* Fold = Fs + ((s - 1) & 1) * S.rmax;  // F'^(s-1)
         float2* Fnew = Fs + (s & 1) * S.rmax;
@@ -574,12 +844,15 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
 #pragma unroll
         for (int v = 0; v < VPT; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
         float errt = 0.f;  // every lane of a team holds the same value
-        for (int kb = 0; kb < nblk; ++kb) {
+        int kb = 0;
+        for (int vp = v0; vp < v1; ++vp) {
+          const int vend = pend[vp];
+          for (; kb < vend; ++kb) {
             const int st = (int)(cseq % (uint32_t)S.stages);
             const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
             const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, g.abort);
-            const int lr0 = kb * S.rows_per_stage;
-            const int rows = min(S.rows_per_stage, nrow - lr0);
+            const int lr0 = kb * rs_;
+            const int rows = min(rs_, nrow - lr0);
             const float* stage = ring + (size_t)st * S.stage_floats;
             for (int j = 0; ok && j < S.rpt; ++j) {
                 const int rr = tm.team + NTEAMS * j;
@@ -588,7 +861,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                 float4 x[VPT];
                 load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
                 const float2 F = Fold[lr];
-                float rs = 0.f;
+                float rsum = 0.f;
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
                     const int col = 4 * (tm.tl + TT * v);
@@ -598,19 +871,19 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                         for (int c = 0; c < 4; ++c) {
                             const float t = ex2(expo(F.x, F.y + comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
                             comp(x[v], c) = t;
-                            rs += t;
+                            rsum += t;
                         }
                     } else {
                         x[v] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
-                rs = team_reduce<TW, float, false>(rs, red, NTEAMS, tm, par);
+                rsum = team_reduce<TW, float, false>(rsum, red, NTEAMS, tm, par);
                 const float ph = Ps[lr];
                 // every lane forms the update (no divergent branch); one lane stores it
-                const float2 Fn = df_sub(F, log2_corr(rs));
+                const float2 Fn = df_sub(F, log2_corr(rsum));
                 if (tm.tl == 0) Fnew[lr] = Fn;
-                errt = fmaf(ph, fabsf(rs - 1.0f), errt);
-                const float d = __fdividef(ph, rs);
+                errt = fmaf(ph, fabsf(rsum - 1.0f), errt);
+                const float d = __fdividef(ph, rsum);
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
                     acc[v].x = fmaf(x[v].x, d, acc[v].x);
@@ -622,46 +895,20 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
             ++cseq;
-        }
-        // CTA combine of the column partials in a fixed order: the first half of the teams
-        // stores, the second half adds its partial onto slot team - NTEAMS/2, then the slots
-        // are summed in order (the buffer holds NTEAMS/2 rows).
-        constexpr int HALF = (NTEAMS + 1) / 2;
-        if (tm.team < HALF) {
-#pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const int col = 4 * (tm.tl + TT * v);
-                if (col < Jp) *reinterpret_cast<float4*>(comb + tm.team * Jp + col) = acc[v];
+          }
+            // end of partition vp: its column partials (teams in order) and row residual
+            if (tm.tl == 0) errf[tm.team] = errt;
+            float* cp = P.colpart + (int64_t)vp * Jp;
+            cta_col_sum<TW, VPT>(comb, acc, J, Jp, tm, [&](int j, float sum) { cp[j] = sum; });
+            if (tid == 0) {
+                float2 e = make_float2(errf[0], 0.f);
+                for (int t = 1; t < NTEAMS; ++t) e = df_add(e, errf[t]);
+                errp[vp] = e;
             }
-        }
-        if (tm.tl == 0) errf[tm.team] = errt;
-        bar_named(CONS_BAR, NC);
-        if (tm.team >= HALF) {
 #pragma unroll
-            for (int v = 0; v < VPT; ++v) {
-                const int col = 4 * (tm.tl + TT * v);
-                if (col < Jp) {
-                    float4* d = reinterpret_cast<float4*>(comb + (tm.team - HALF) * Jp + col);
-                    float4 o = *d;
-                    o.x += acc[v].x;
-                    o.y += acc[v].y;
-                    o.z += acc[v].z;
-                    o.w += acc[v].w;
-                    *d = o;
-                }
-            }
-        }
-        bar_named(CONS_BAR, NC);
-        for (int j = tid; j < J; j += NC) {
-            float sum = comb[j];
-            for (int t = 1; t < HALF; ++t) sum += comb[t * Jp + j];
-            P.colpart[(int64_t)b * Jp + j] = sum;
-        }
-        float2* errp = reinterpret_cast<float2*>(P.errpart);
-        if (tid == 0) {
-            float2 e = make_float2(errf[0], 0.f);
-            for (int t = 1; t < NTEAMS; ++t) e = df_add(e, errf[t]);
-            errp[b] = e;
+            for (int v = 0; v < VPT; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            errt = 0.f;
+            if (vp + 1 < v1) bar_named(CONS_BAR, NC);  // errf is read by thread 0 above
         }
         OTA_BARRIER();
         // Loop test on pi^(s-1) (warp 0; every CTA forms the same total in the same order)
@@ -669,7 +916,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
         // for a stop.  All sums here are FP32 pairs: no FP64 in the per-sweep path.
         if (warp == 0) {
             float2 e = make_float2(0.f, 0.f);
-            for (int bb = lane; bb < nb; bb += 32) e = df_add2(e, errp[bb]);
+            for (int bb = lane; bb < V; bb += 32) e = df_add2(e, errp[bb]);
             e = warp_sum_df(e);
             if (lane == 0) {
                 const double ed = (double)e.x + (double)e.y;
@@ -688,7 +935,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             const int gw = b * (NCW - 1) + (warp - 1), nw = nb * (NCW - 1);
             for (int j = gw; warp > 0 && j < J; j += nw) {
                 float2 sum = make_float2(0.f, 0.f);
-                for (int bb = lane; bb < nb; bb += 32) sum = df_add(sum, P.colpart[(int64_t)bb * Jp + j]);
+                for (int bb = lane; bb < V; bb += 32) sum = df_add(sum, P.colpart[(int64_t)bb * Jp + j]);
                 sum = warp_sum_df(sum);
                 if (lane == 0) {
                     if (!(sum.x > 0.f) || !isfinite(sum.x)) {
@@ -706,6 +953,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             if (P.F_out)
                 for (int r = tid; r < nrow; r += NC) P.F_out[r0 + r] = Fold[r];
             *ret_par = (s - 1) & 1;
+            if (P.fpart) sk_finalize_sweep<TW, VPT>(P, S, sh, dyn, r0, nrow, v0, v1, Fold, cseq, g.abort);
             if (tid == 0) s_stop = 1;
             return true;
         }
