@@ -179,6 +179,8 @@ __device__ __forceinline__ bool bt_instance(const BatchParams& B, int ii, const 
     P.pi_ld = D.pi_ld;
     P.f_nat = D.f_out;
     P.eps_ln2 = D.eps_ln2;
+    P.F_in = nullptr;
+    P.G_in = nullptr;
     const StreamCfg S = D.S;
     uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
     uint64_t* empty = full + MAX_STAGES;

@@ -76,10 +76,10 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve(SolveParams P, Strea
 // ------------------------------------------------------------------------------------------
 __global__ void sk_finalize_cols(const double2* __restrict__ fpart, int nb, int Jp, int J,
                                  const float* __restrict__ q, const DevScalars* sc,
-                                 const LoopState* st, const double* G, double eps_ln2,
+                                 const LoopState* st, const double* G, int g_by_parity, double eps_ln2,
                                  double* g_out, double* rrh_load, double2* cols) {
     if (st->status != DEV_OK) return;
-    G += (st->iters & 1) * Jp;  // G^k of the returned plan
+    if (g_by_parity) G += (st->iters & 1) * Jp;  // G^k of the returned plan
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -220,9 +220,28 @@ struct SolveBufs {
     double2* fpart;   // [nb][Jp]
 };
 
-// Enqueue the whole solve; the caller copies B.summ back.
+// What one launch of the persistent kernel does (besides the full solve).
+struct SolveMode {
+    int init = 0;                // iteration 1 only, no finalize; F'^1 -> F_out, G^1 stays in B.G + Jp
+    float2* F_out = nullptr;
+    const float2* F_in = nullptr;  // finalize only, on these potentials (F' pairs, G log2 units)
+    const double* G_in = nullptr;
+    int iters = 0;               // reported with a finalize-only launch
+    double err = 0.0;
+    int converged = 0;
+};
+
+__global__ void sk_set_loop(LoopState* ls, int iters, double err, int converged) {
+    if (threadIdx.x == 0) {
+        ls->iters = iters;
+        ls->err = err;
+        ls->converged = converged;
+    }
+}
+
+// Enqueue the whole solve (or the part `mode` asks for); the caller copies B.summ back.
 cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunch& LL, const SolveBufs& B,
-                          long long spin, cudaStream_t s, ot_assoc_ctx* ctx) {
+                          long long spin, cudaStream_t s, ot_assoc_ctx* ctx, const SolveMode& mode = SolveMode()) {
     const int J = a.J;
     const int64_t I = a.I;
     const int Jp = (int)round_up(J, 4);
@@ -232,6 +251,7 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
     if (ctx) timing_mark(ctx, 0, s);
     cudaError_t e = cudaMemsetAsync(B.sc, 0, 1024, s);  // DevScalars, LoopState, summary
     if (e != cudaSuccess) return e;
+    if (mode.F_in) sk_set_loop<<<1, 32, 0, s>>>(B.ls, mode.iters, mode.err, mode.converged);
     SolveParams P;
     P.C = a.C;
     P.ld = a.ld;
@@ -246,21 +266,23 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
     P.sc = B.sc;
     P.st = B.ls;
     P.G = B.G;
-    P.F_out = nullptr;
+    P.F_out = mode.F_out;
     P.colpart = (float*)B.colpart;
     P.errpart = B.errpart;
     P.k = k;
     P.k_hi = k_hi;
     P.k_lo = k_lo;
-    P.tol = a.tol;
-    P.max_iter = a.max_iter;
+    P.tol = mode.init ? 0.0 : a.tol;
+    P.max_iter = mode.init ? 1 : a.max_iter;
     P.spin = spin;
-    P.fpart = B.fpart;
+    P.fpart = mode.init ? nullptr : B.fpart;
     P.epart = B.errpart + LL.V;
     P.pi = a.out->pi;
     P.pi_ld = a.out->pi_ld > 0 ? a.out->pi_ld : J;
     P.f_nat = a.out->f;
     P.eps_ln2 = a.eps * LN2;
+    P.F_in = mode.F_in;
+    P.G_in = mode.G_in;
     if (ctx) timing_mark(ctx, 1, s);
     {
         void* args[] = {&P, (void*)&LL.cfg};
@@ -268,12 +290,35 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
         if (e != cudaSuccess) return e;
     }
     if (ctx) timing_mark(ctx, 2, s);
-    const int nb_cols = (int)std::max<int64_t>(1, std::min<int64_t>((J + 15) / 16, 1024));
-    sk_finalize_cols<<<nb_cols, 512, 0, s>>>(B.fpart, LL.V, Jp, J, a.q, B.sc, B.ls, B.G, a.eps * LN2, a.out->g,
-                                             a.out->rrh_load, B.cols);
-    sk_summary<<<1, 256, 0, s>>>(P.epart, LL.V, B.cols, J, B.sc, B.ls, B.summ);
+    if (!mode.init) {
+        const int nb_cols = (int)std::max<int64_t>(1, std::min<int64_t>((J + 15) / 16, 1024));
+        const double* G = mode.G_in ? mode.G_in : B.G;
+        sk_finalize_cols<<<nb_cols, 512, 0, s>>>(B.fpart, LL.V, Jp, J, a.q, B.sc, B.ls, G, mode.G_in ? 0 : 1,
+                                                 a.eps * LN2, a.out->g, a.out->rrh_load, B.cols);
+        sk_summary<<<1, 256, 0, s>>>(P.epart, LL.V, B.cols, J, B.sc, B.ls, B.summ);
+    }
     if (ctx) timing_mark(ctx, 3, s);
     return cudaGetLastError();
+}
+
+// Scratch of a solve in context memory.
+ot_status solve_bufs(ot_assoc_ctx* ctx, const LoopLaunch& LL, int Jp, SolveBufs* B) {
+    ot_status st = OT_OK;
+    B->colpart = scratch(ctx, SLOT_COLPART, sizeof(float2) * (size_t)LL.V * Jp, &st);
+    if (st) return st;
+    B->fpart = (double2*)scratch(ctx, SLOT_FINPART, sizeof(double2) * (size_t)LL.V * Jp, &st);
+    if (st) return st;
+    B->G = (double*)scratch(ctx, SLOT_G, sizeof(double) * 3 * (size_t)Jp, &st);
+    if (st) return st;
+    B->errpart = (double*)scratch(ctx, SLOT_ERRPART, sizeof(double) * 2 * (size_t)LL.V, &st);
+    if (st) return st;
+    char* state = (char*)scratch(ctx, SLOT_STATE, 4096 + sizeof(double2) * (size_t)Jp, &st);
+    if (st) return st;
+    B->sc = (DevScalars*)state;
+    B->ls = (LoopState*)(state + 256);
+    B->summ = (SolveSummary*)(state + 512);
+    B->cols = (double2*)(state + 4096);
+    return OT_OK;
 }
 
 }  // namespace
@@ -289,20 +334,8 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
     st = plan_solve(kk, I, Jp, a.ld, ctx->num_sms, 1 << 30, &LL);
     if (st) return set_error(ctx, st, "solver does not fit the shared memory (I=%lld J=%d)", (long long)I, J);
     SolveBufs B;
-    B.colpart = scratch(ctx, SLOT_COLPART, sizeof(float2) * (size_t)LL.V * Jp, &st);
+    st = solve_bufs(ctx, LL, Jp, &B);
     if (st) return st;
-    B.fpart = (double2*)scratch(ctx, SLOT_FINPART, sizeof(double2) * (size_t)LL.V * Jp, &st);
-    if (st) return st;
-    B.G = (double*)scratch(ctx, SLOT_G, sizeof(double) * 3 * (size_t)Jp, &st);
-    if (st) return st;
-    B.errpart = (double*)scratch(ctx, SLOT_ERRPART, sizeof(double) * 2 * (size_t)LL.V, &st);
-    if (st) return st;
-    char* state = (char*)scratch(ctx, SLOT_STATE, 4096 + sizeof(double2) * (size_t)Jp, &st);
-    if (st) return st;
-    B.sc = (DevScalars*)state;
-    B.ls = (LoopState*)(state + 256);
-    B.summ = (SolveSummary*)(state + 512);
-    B.cols = (double2*)(state + 4096);
     SolveSummary* hsum = (SolveSummary*)host_staging(ctx, sizeof(SolveSummary), &st);
     if (st) return st;
     ctx->last_timings.valid = 0;
@@ -316,6 +349,70 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
     if (e != cudaSuccess) return cuda_error(ctx, e, "solve");
     *sum_host = *hsum;
     timing_collect(ctx, hsum->iters);
+    return OT_OK;
+}
+
+// Iteration 1 of the FP32 log-domain solver (the exact first sweep and the b-update):
+// F'^1 (pairs) into F_out, G^1 (log2 units) into G_out.  Synchronises; *status gets the
+// device status (invalid input is reported here).
+ot_status f32_first_iteration(ot_assoc_ctx* ctx, const SolveArgs& a, float2* F_out, double* G_out, int* status) {
+    ot_status st = OT_OK;
+    const int J = a.J;
+    const int Jp = (int)round_up(J, 4);
+    Kernels kk;
+    if (!pick_kernels(J, &kk)) return set_error(ctx, OT_EUNSUPPORTED, "J=%d above 8192", J);
+    LoopLaunch LL;
+    st = plan_solve(kk, a.I, Jp, a.ld, ctx->num_sms, 1 << 30, &LL);
+    if (st) return set_error(ctx, st, "solver does not fit the shared memory (I=%lld J=%d)", (long long)a.I, J);
+    SolveBufs B;
+    st = solve_bufs(ctx, LL, Jp, &B);
+    if (st) return st;
+    SolveMode m;
+    m.init = 1;
+    m.F_out = F_out;
+    cudaStream_t s = a.stream;
+    cudaError_t e = enqueue_solve(a, kk, LL, B, ctx->spin_limit, s, nullptr, m);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(G_out, B.G + Jp, sizeof(double) * Jp, cudaMemcpyDeviceToDevice, s);
+    LoopState* h = (LoopState*)host_staging(ctx, sizeof(LoopState), &st);
+    if (st) return st;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, B.ls, sizeof(LoopState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "first iteration");
+    ctx->launches += 1;
+    *status = h->status;
+    return OT_OK;
+}
+
+// Finalize on given potentials (F' pairs, G log2 units): plan, f, g, loads and FP64 summary
+// as the full solve gives them; iters / err / converged are reported as passed.
+ot_status f32_finalize_on(ot_assoc_ctx* ctx, const SolveArgs& a, const float2* F_in, const double* G_in, int iters,
+                          double err, int converged, SolveSummary* sum_host) {
+    ot_status st = OT_OK;
+    const int J = a.J;
+    const int Jp = (int)round_up(J, 4);
+    Kernels kk;
+    if (!pick_kernels(J, &kk)) return set_error(ctx, OT_EUNSUPPORTED, "J=%d above 8192", J);
+    LoopLaunch LL;
+    st = plan_solve(kk, a.I, Jp, a.ld, ctx->num_sms, 1 << 30, &LL);
+    if (st) return set_error(ctx, st, "solver does not fit the shared memory (I=%lld J=%d)", (long long)a.I, J);
+    SolveBufs B;
+    st = solve_bufs(ctx, LL, Jp, &B);
+    if (st) return st;
+    SolveSummary* hsum = (SolveSummary*)host_staging(ctx, sizeof(SolveSummary), &st);
+    if (st) return st;
+    SolveMode m;
+    m.F_in = F_in;
+    m.G_in = G_in;
+    m.iters = iters;
+    m.err = err;
+    m.converged = converged;
+    cudaStream_t s = a.stream;
+    cudaError_t e = enqueue_solve(a, kk, LL, B, ctx->spin_limit, s, nullptr, m);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hsum, B.summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "finalize");
+    ctx->launches += 4;
+    *sum_host = *hsum;
     return OT_OK;
 }
 

@@ -128,6 +128,10 @@ ot_status launch_solve_f64(ot_assoc_ctx* ctx, const SolveArgs64& a, SolveSummary
 
 ot_status launch_solve_lowp(ot_assoc_ctx* ctx, const SolveArgs& a, int format, double absorb_log2,
                             SolveSummary* sum_host);
+// Pieces of the FP32 solver the stored-kernel form builds on (k_sinkhorn.cu).
+ot_status f32_first_iteration(ot_assoc_ctx* ctx, const SolveArgs& a, float2* F_out, double* G_out, int* status);
+ot_status f32_finalize_on(ot_assoc_ctx* ctx, const SolveArgs& a, const float2* F_in, const double* G_in, int iters,
+                          double err, int converged, SolveSummary* sum_host);
 
 ot_status launch_rates(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const float* P, int64_t I,
                        int J, double N0, double W, float* R, int64_t ld_r, cudaStream_t s);

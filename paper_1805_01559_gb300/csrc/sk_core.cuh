@@ -97,7 +97,7 @@ struct StreamCfg {
     int rows_per_stage;  // NTEAMS * rpt
     int rpt;             // rows per team per stage
     int stages;
-    int stage_floats;    // rows_per_stage * ld
+    int stage_floats;    // rows_per_stage * ld (elements of the streamed matrix)
     int rmax;            // most rows any CTA owns
     int off_G;           // byte offsets inside dynamic smem
     int off_F;
@@ -152,8 +152,9 @@ __device__ __forceinline__ void load_row_smem(const float* row, int J, int tl, f
 
 // Producer: stream the CTA's row blocks sweep after sweep until the consumers raise s_stop,
 // then wait for every copy still in flight before leaving.
-__device__ __forceinline__ void stream_rows_producer(const float* C, int64_t ld, int64_t r0, int64_t r1,
-                                                     const StreamCfg& S, float* ring, uint64_t* full,
+template <typename T>
+__device__ __forceinline__ void stream_rows_producer(const T* C, int64_t ld, int64_t r0, int64_t r1,
+                                                     const StreamCfg& S, T* ring, uint64_t* full,
                                                      uint64_t* empty, volatile int* s_stop, int* status,
                                                      long long spin) {
     const int nblk = (int)((r1 - r0 + S.rows_per_stage - 1) / S.rows_per_stage);
@@ -179,7 +180,7 @@ __device__ __forceinline__ void stream_rows_producer(const float* C, int64_t ld,
             if (*s_stop) { stop = true; break; }
             const int64_t row0 = r0 + (int64_t)k * S.rows_per_stage;
             const int rows = (int)min((int64_t)S.rows_per_stage, r1 - row0);
-            const uint32_t bytes = (uint32_t)(rows * ld * (int64_t)sizeof(float));
+            const uint32_t bytes = (uint32_t)(rows * ld * (int64_t)sizeof(T));
             mbar_arrive_expect_tx(&full[st], bytes);
             bulk_g2s(ring + (size_t)st * S.stage_floats, C + row0 * ld, bytes, &full[st]);
             ++seq;
@@ -230,6 +231,10 @@ struct SolveParams {
     int64_t pi_ld;
     double* f_nat;    // [I] f_i = eps ln2 (F'_i + log2 p_i), or nullptr
     double eps_ln2;
+    // Finalize only (F_in not null): no iteration; the finalize sweep runs on the caller's
+    // potentials F' (pairs) and G (log2 units).
+    const float2* F_in;  // [I]
+    const double* G_in;  // [Jp]
 };
 
 // Row partitions.  The I rows form B = ceil(I / rs) stage blocks of rs rows; partition v of V
@@ -270,9 +275,9 @@ __host__ __device__ __forceinline__ int parts_for(int64_t I, int rs) {
 // by (I, J, ld, stage target) whatever nb is.  Returns false when a CTA's rows do not fit
 // next to two stages.
 inline bool plan_stage(int nteams, int64_t I, int Jp, int64_t ld, int nb, int stage_target, size_t budget,
-                       StreamCfg* S, size_t* smem, int* Vout) {
+                       StreamCfg* S, size_t* smem, int* Vout, int esize = 4) {
     const size_t comb = (size_t)((nteams + 1) / 2) * Jp * sizeof(float);
-    const size_t row_bytes = (size_t)ld * sizeof(float);
+    const size_t row_bytes = (size_t)ld * esize;
     const int rpt = (int)(stage_target / ((size_t)nteams * row_bytes) > 1 ? stage_target / ((size_t)nteams * row_bytes)
                                                                            : 1);
     const int rs = nteams * rpt;
@@ -295,7 +300,7 @@ inline bool plan_stage(int nteams, int64_t I, int Jp, int64_t ld, int nb, int st
     S->rpt = rpt;
     S->rows_per_stage = rs;
     S->stages = stages;
-    S->stage_floats = (int)(stage / sizeof(float));
+    S->stage_floats = (int)(stage / esize);
     S->rmax = (int)(rmax > 0 ? rmax : 1);
     S->off_G = (int)off_G;
     S->off_F = (int)off_F;
@@ -650,9 +655,18 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
         bar_named(CONS_BAR, NC);
     }
     const Team<TW> tm;
+    uint32_t cseq = 0;
+    if (P.F_in) {  // finalize only
+        for (int r = tid; r < nrow; r += NC) Fs[r] = P.F_in[r0 + r];
+        load_G_smem(P.G_in, J, Jp, Gs, tid, NC);
+        bar_named(CONS_BAR, NC);
+        *ret_par = 0;
+        sk_finalize_sweep<TW, VPT>(P, S, sh, dyn, r0, nrow, v0, v1, Fs, cseq, g.abort);
+        if (tid == 0) s_stop = 1;
+        return true;
+    }
     load_G_smem(P.G, J, Jp, Gs, tid, NC);
     bar_named(CONS_BAR, NC);
-    uint32_t cseq = 0;
     int par = 0;
 
     // ---- sweep 1: exact log-domain iteration ------------------------------------------
