@@ -350,6 +350,83 @@ ot_status ot_assoc_tuning_set(ot_assoc_ctx* ctx, int32_t bucket, int32_t gsize, 
 int32_t ot_assoc_bucket(int64_t I, int32_t J);
 
 
+/* ---------------------------------------------------------------------------------------
+ * Serving (the paper has no counterpart: a service of the library around Algorithm 1).
+ * Cells are registered once and keep their cost C, marginals p, q and potentials f, g
+ * resident in HBM.  A request is one new time instance of a cell: new gains (caller-given,
+ * or the cell's devices moved by dt on the device, for simulation), from which the rates
+ * (Sec. II-A) and C = 1/(mu R) are rebuilt in place, then a solve warm-started from the
+ * cell's previous g.  One persistent launch serves all cells: its CTAs form groups, each
+ * group takes the next published request (the host appends while the launch runs), so
+ * requests that arrive while others are on the GPU start as soon as a group is free.
+ * Requests of one cell run in submission order; results depend only on the cell's data,
+ * so they are the same alone and in any mix.  Admission: a cell is accepted only if its
+ * resident footprint fits the server's HBM budget (OT_EBUSY otherwise).  J <= 1024.
+ * ------------------------------------------------------------------------------------- */
+typedef struct ot_assoc_server ot_assoc_server;
+
+typedef struct {
+    int32_t group_ctas;  /* CTAs per group (divides the SM count); 0 = 8 */
+    int32_t max_J;       /* largest J of any cell (group scratch); 0 = 1024 */
+    double idle_us;      /* a group with no work waits this long before the launch may end; 0 = 200 */
+    size_t hbm_budget;   /* bytes of resident cell state; 0 = no limit */
+} ot_assoc_server_config;
+
+typedef struct {
+    int64_t I;
+    int32_t J;
+    int32_t warm_start;  /* != 0: each request starts from the previous request's g */
+    double eps, tol;     /* tol < 0 = 1e-6 */
+    int32_t max_iter;    /* <= 0 = 2000 */
+    int32_t reserved;
+    double mu, N0, W_hz; /* rates and cost (Sec. II-A, Sec. IV) */
+    const float* P;      /* [host] J transmit powers */
+    const float* p;      /* [host] I traffic (> 0) */
+    const float* q;      /* [host] J RRH marginal (> 0, sum q = sum p) */
+    /* drifting cell (all NULL: every request brings its gains) */
+    const double* dev_xy;    /* [host] I x 2 device positions (m) */
+    const double* dev_v;     /* [host] I x 2 velocities (m/s) */
+    const float* rrh_xy;     /* [host] J x 2 RRH positions (m) */
+    const float* shadow_db;  /* [host] I x J shadowing (dB), fixed per link */
+    double side_m;           /* devices reflect at the walls of [0, side]^2 */
+} ot_assoc_cell_desc;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t cell;
+    int32_t status;        /* OT_OK, OT_NOT_CONVERGED, OT_EINVAL, OT_ETIMEOUT */
+    int32_t iters;
+    int32_t reserved;
+    double transport_cost, marg_err_row, marg_err_col;
+    double t_submit_us, t_start_us, t_done_us;  /* host steady clock: submitted, published, seen done */
+} ot_assoc_server_result;
+
+typedef struct {
+    size_t resident_bytes;
+    int32_t cells, groups, group_ctas, waiting, inflight, reserved;
+    uint64_t launches;
+} ot_assoc_server_stats_t;
+
+ot_status ot_assoc_server_create(ot_assoc_ctx* ctx, const ot_assoc_server_config* cfg, ot_assoc_server** out);
+/* Waits for work in flight, frees everything.  Destroy before the context. */
+void ot_assoc_server_destroy(ot_assoc_server* s);
+/* Register a cell (its arrays are copied); OT_EBUSY when it does not fit the budget. */
+ot_status ot_assoc_server_add_cell(ot_assoc_server* s, const ot_assoc_cell_desc* d, int32_t* cell_id);
+/* Submit a time instance: gains G [device] I x J (16-byte aligned rows, ld_g % 4 == 0; 0 =
+ * J), or G = NULL and dt seconds of motion for a drifting cell.  G must stay valid until
+ * the request's result is polled.  Returns at once (the scheduler makes progress). */
+ot_status ot_assoc_server_submit(ot_assoc_server* s, int32_t cell, const float* G, int64_t ld_g, double dt,
+                                 uint64_t* ticket);
+/* Make progress and take up to max finished results [host array]; *n gets how many. */
+ot_status ot_assoc_server_poll(ot_assoc_server* s, ot_assoc_server_result* out, int32_t max, int32_t* n);
+/* Make progress until nothing is pending (results stay available to poll). */
+ot_status ot_assoc_server_drain(ot_assoc_server* s, double timeout_s);
+/* Device pointers of a cell's resident state (valid while the server lives; read only
+ * between requests of that cell). */
+ot_status ot_assoc_server_cell_state(const ot_assoc_server* s, int32_t cell, const float** C, double** f,
+                                     double** g, double** rrh_load);
+ot_status ot_assoc_server_stats(const ot_assoc_server* s, ot_assoc_server_stats_t* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -546,3 +546,182 @@ Context.autotune = _ctx_autotune
 Context.tuning = _ctx_tuning
 Context.set_tuning = _ctx_set_tuning
 Context.batch = lambda self, instances, graph=True: Batch(self, instances, graph)
+
+
+# ---- serving ------------------------------------------------------------------------------
+class ot_assoc_server_config(ctypes.Structure):
+    _fields_ = [("group_ctas", ctypes.c_int32), ("max_J", ctypes.c_int32), ("idle_us", ctypes.c_double),
+                ("hbm_budget", ctypes.c_size_t)]
+
+
+class ot_assoc_cell_desc(ctypes.Structure):
+    _fields_ = [
+        ("I", ctypes.c_int64), ("J", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+        ("eps", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("mu", ctypes.c_double), ("N0", ctypes.c_double), ("W_hz", ctypes.c_double),
+        ("P", ctypes.c_void_p), ("p", ctypes.c_void_p), ("q", ctypes.c_void_p),
+        ("dev_xy", ctypes.c_void_p), ("dev_v", ctypes.c_void_p), ("rrh_xy", ctypes.c_void_p),
+        ("shadow_db", ctypes.c_void_p), ("side_m", ctypes.c_double),
+    ]
+
+
+class ot_assoc_server_result(ctypes.Structure):
+    _fields_ = [
+        ("ticket", ctypes.c_uint64), ("cell", ctypes.c_int32), ("status", ctypes.c_int32),
+        ("iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("transport_cost", ctypes.c_double),
+        ("marg_err_row", ctypes.c_double), ("marg_err_col", ctypes.c_double), ("t_submit_us", ctypes.c_double),
+        ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double),
+    ]
+
+
+class ot_assoc_server_stats_t(ctypes.Structure):
+    _fields_ = [("resident_bytes", ctypes.c_size_t), ("cells", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("group_ctas", ctypes.c_int32), ("waiting", ctypes.c_int32), ("inflight", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("launches", ctypes.c_uint64)]
+
+
+SIGNATURES.update({
+    "ot_assoc_server_create": (ctypes.c_int, [_VP, ctypes.POINTER(ot_assoc_server_config), ctypes.POINTER(_VP)]),
+    "ot_assoc_server_destroy": (None, [_VP]),
+    "ot_assoc_server_add_cell": (ctypes.c_int, [_VP, ctypes.POINTER(ot_assoc_cell_desc),
+                                                ctypes.POINTER(ctypes.c_int32)]),
+    "ot_assoc_server_submit": (ctypes.c_int, [_VP, _I32, _VP, _I64, _D, ctypes.POINTER(ctypes.c_uint64)]),
+    "ot_assoc_server_poll": (ctypes.c_int, [_VP, ctypes.POINTER(ot_assoc_server_result), _I32,
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "ot_assoc_server_drain": (ctypes.c_int, [_VP, _D]),
+    "ot_assoc_server_cell_state": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                                  ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "ot_assoc_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ot_assoc_server_stats_t)]),
+})
+if _lib is not None:  # already loaded: register the new entry points
+    for _name in ("ot_assoc_server_create", "ot_assoc_server_destroy", "ot_assoc_server_add_cell",
+                  "ot_assoc_server_submit", "ot_assoc_server_poll", "ot_assoc_server_drain",
+                  "ot_assoc_server_cell_state", "ot_assoc_server_stats"):
+        _fn = getattr(_lib, _name)
+        _fn.restype, _fn.argtypes = SIGNATURES[_name]
+
+
+@dataclasses.dataclass
+class ServerResult:
+    ticket: int
+    cell: int
+    status: int
+    iters: int
+    transport_cost: float
+    marg_err_row: float
+    marg_err_col: float
+    t_submit_us: float
+    t_start_us: float
+    t_done_us: float
+
+    @property
+    def latency_us(self) -> float:
+        return self.t_done_us - self.t_submit_us
+
+
+class Server:
+    """ot_assoc_server: resident cells, continuously batched warm-started solves."""
+
+    def __init__(self, ctx: "Context", group_ctas: int = 8, max_J: int = 1024, idle_us: float = 200.0,
+                 hbm_budget: int = 0):
+        self._ctx = ctx
+        self._L = ctx._L
+        cfg = ot_assoc_server_config(int(group_ctas), int(max_J), float(idle_us), int(hbm_budget))
+        h = ctypes.c_void_p()
+        ctx._check(self._L.ot_assoc_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}  # host arrays and request gains kept alive
+
+    def add_cell(self, I, J, eps, P, p, q, mu, N0, W_hz, tol=1e-6, max_iter=2000, warm_start=True,
+                 dev_xy=None, dev_v=None, rrh_xy=None, shadow_db=None, side_m=0.0) -> int:
+        import numpy as np
+        arrs = {"P": np.ascontiguousarray(P, np.float32), "p": np.ascontiguousarray(p, np.float32),
+                "q": np.ascontiguousarray(q, np.float32)}
+        if dev_xy is not None:
+            arrs.update(dev_xy=np.ascontiguousarray(dev_xy, np.float64), dev_v=np.ascontiguousarray(dev_v, np.float64),
+                        rrh_xy=np.ascontiguousarray(rrh_xy, np.float32),
+                        shadow_db=np.ascontiguousarray(shadow_db, np.float32))
+        d = ot_assoc_cell_desc()
+        d.I, d.J, d.warm_start = int(I), int(J), 1 if warm_start else 0
+        d.eps, d.tol, d.max_iter = float(eps), float(tol), int(max_iter)
+        d.mu, d.N0, d.W_hz = float(mu), float(N0), float(W_hz)
+        for k, v in arrs.items():
+            setattr(d, k, v.ctypes.data)
+        d.side_m = float(side_m)
+        cid = ctypes.c_int32(-1)
+        self._ctx._check(self._L.ot_assoc_server_add_cell(self._h, ctypes.byref(d), ctypes.byref(cid)))
+        return cid.value
+
+    def submit(self, cell: int, G: Optional[torch.Tensor] = None, dt: float = 0.0) -> int:
+        t = ctypes.c_uint64(0)
+        if G is not None:
+            _need(G, torch.float32, "G", 2)
+        self._ctx._check(self._L.ot_assoc_server_submit(self._h, int(cell), _ptr(G), G.stride(0) if G is not None else 0,
+                                                        float(dt), ctypes.byref(t)))
+        if G is not None:
+            self._keep[t.value] = G
+        return t.value
+
+    def poll(self, max_results: int = 256) -> list:
+        arr = (ot_assoc_server_result * max_results)()
+        n = ctypes.c_int32(0)
+        self._ctx._check(self._L.ot_assoc_server_poll(self._h, arr, int(max_results), ctypes.byref(n)))
+        out = []
+        for k in range(n.value):
+            r = arr[k]
+            self._keep.pop(r.ticket, None)
+            out.append(ServerResult(r.ticket, r.cell, r.status, r.iters, r.transport_cost, r.marg_err_row,
+                                    r.marg_err_col, r.t_submit_us, r.t_start_us, r.t_done_us))
+        return out
+
+    def drain(self, timeout_s: float = 60.0) -> list:
+        self._ctx._check(self._L.ot_assoc_server_drain(self._h, float(timeout_s)))
+        out = []
+        while True:
+            got = self.poll()
+            out += got
+            if len(got) == 0:
+                return out
+
+    def cell_state(self, cell: int, I: int, J: int):
+        """(C, f, g, rho) of a cell: copies of the resident device buffers."""
+        C, f, g, rho = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        self._ctx._check(self._L.ot_assoc_server_cell_state(self._h, int(cell), ctypes.byref(C), ctypes.byref(f),
+                                                            ctypes.byref(g), ctypes.byref(rho)))
+        ldc = (J + 3) // 4 * 4
+        torch.cuda.synchronize()
+        Cv = _device_view(C.value, (I, ldc), "<f4")[:, :J].clone()
+        return (Cv, _device_view(f.value, (I,), "<f8").clone(), _device_view(g.value, (J,), "<f8").clone(),
+                _device_view(rho.value, (J,), "<f8").clone())
+
+    def stats(self) -> dict:
+        s = ot_assoc_server_stats_t()
+        self._ctx._check(self._L.ot_assoc_server_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ot_assoc_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DevBuf:
+    """A library-owned device buffer described by the CUDA array interface."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _device_view(ptr: int, shape, typestr: str) -> torch.Tensor:
+    return torch.as_tensor(_DevBuf(ptr, shape, typestr), device="cuda")
+
+
+Context.server = lambda self, **kw: Server(self, **kw)
