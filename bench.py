@@ -220,8 +220,10 @@ def run_gpu(args):
             if record:
                 t = ctx.last_timings()
                 if t["valid"]:
+                    # the persistent kernel reads C once per iteration, once more to test the
+                    # last plan, and once in the finalize sweep
                     loop_ms.append(t["loop_ms"])
-                    loop_bytes.append(4.0 * I * J * t["sweeps"])
+                    loop_bytes.append(4.0 * I * J * (t["sweeps"] + 2))
         return cells, its
 
     for _ in range(args.warmup):
@@ -304,11 +306,12 @@ def run_gpu(args):
                        "iters": iters_seen[0] if iters_seen else None,
                        "l2": "inputs larger than L2 (C and G 160 MB each > 126 MB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "sk_loop (persistent Sinkhorn sweep)",
+            "roofline": {"bound": "hbm", "kernel": "sk_solve (persistent Sinkhorn: setup, sweeps, finalize sweep)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "peak_kind": peak_kind,
-                         "bytes_per_cell_iter": 4, "launches_timed": len(loop_ms)},
+                         "bytes_per_cell_iter": 4, "reads_of_C_per_launch": "iters + 2",
+                         "launches_timed": len(loop_ms)},
             "e2e": {"value": e2e_cells / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -347,6 +350,272 @@ def run_profile_solve(args):
     return 0
 
 
+# ------------------------------------------------------------------------------ other workloads
+# The default line above is the headline benchmark.  These modes measure the other
+# configurations (one JSON line each, "workload" names them); inputs are generated on the host
+# in a process pool started before any CUDA call.
+def _pool(n: int):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(n)
+
+
+def _gen_c3(args):
+    from paper_1805_01559_gb300 import instances as ins
+    I, J, seed = args
+    x = ins.config3_cell(I, J, seed, dtype=np.float32)
+    return (np.ascontiguousarray(x.G, np.float32), x.P.astype(np.float32), x.lam.astype(np.float32),
+            x.q.astype(np.float32), x.N0, x.W_hz, x.mu)
+
+
+_C4 = {}
+
+
+def _gen_c4_block(args):
+    from paper_1805_01559_gb300 import instances as ins
+    seed, I, J, block, b = args
+    key = (seed, I, J, block)
+    if key not in _C4:
+        _C4.clear()
+        _C4[key] = ins.config4_blocked(seed, I, J, block)
+    return b, _C4[key].gains_block(b)
+
+
+def _gen_c5(args):
+    from multiprocessing import shared_memory
+    from paper_1805_01559_gb300 import instances as ins
+    I, J, seed = args
+    c = ins.serving_cell(I, J, seed)
+    sh = np.ascontiguousarray(c.shadow_db, np.float32)
+    shm = shared_memory.SharedMemory(create=True, size=sh.nbytes)
+    np.ndarray(sh.shape, np.float32, buffer=shm.buf)[:] = sh
+    name = shm.name
+    shm.close()
+    return dict(I=I, J=J, dev_xy=c.dev_xy, vel=c.vel, rrh_xy=c.rrh_xy.astype(np.float32), lam=c.lam, q=c.q,
+                side=c.side, shm=name)
+
+
+def _timed(fn, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)
+
+
+def run_c3(args):
+    """256 ragged instances (I ~ U{2000..60000}, J ~ U{64..1024}, channel as the 1000 x 50
+    configuration), eps = 0.05 median(C) each: the batched persistent launch (captured graph)
+    against the per-instance solver loop, same tolerance."""
+    from paper_1805_01559_gb300 import instances as ins
+    shapes = ins.config3_shapes()[: args.c3_instances]
+    pool = _pool(min(16, os.cpu_count() or 1))
+    import torch
+    from paper_1805_01559_gb300 import binding
+    ctx = binding.Context(0)
+    dev = torch.device("cuda", 0)
+    items = []
+    t0 = time.perf_counter()
+    for (G, P, lam, q, N0, W, mu), (I, J, _) in zip(pool.imap(_gen_c3, shapes, chunksize=1), shapes):
+        Gd = torch.from_numpy(G).to(dev)
+        R = ctx.build_rates(Gd, torch.from_numpy(P).to(dev), N0, W)
+        ld = (J + 3) // 4 * 4
+        C = torch.empty((I, ld), dtype=torch.float32, device=dev)[:, :J]
+        _, med = ctx.build_cost(R, mu, eps_rel=1.0, C_out=C)
+        del Gd, R
+        items.append(dict(C=C, p=torch.from_numpy(lam).to(dev), q=torch.from_numpy(q).to(dev), eps=0.05 * med))
+    pool.close()
+    gen_s = time.perf_counter() - t0
+    s = torch.cuda.current_stream()
+    mk = lambda: [binding.Instance(C=x["C"], p=x["p"], q=x["q"], eps=x["eps"], tol=TOL, max_iter=MAX_ITER)
+                  for x in items]
+    cells = [x["C"].shape[0] * x["C"].shape[1] for x in items]
+
+    def plain():
+        return [ctx.solve_cost(x["C"], x["p"], x["q"], x["eps"], tol=TOL, max_iter=MAX_ITER).iters for x in items]
+
+    res = {}
+    for name in ("plain", "batched", "batched_tuned"):
+        if name == "batched_tuned":
+            if not args.autotune:
+                continue
+            t_tune = time.perf_counter()
+            ctx.autotune(mk(), iters=6)
+            res["tune_s"] = time.perf_counter() - t_tune
+        b = ctx.batch(mk(), graph=True) if name != "plain" else None
+        run = plain if b is None else (lambda: [r.iters for r in b.run()])
+        for _ in range(args.warmup):
+            run()
+        ms_all, its = [], None
+        for _ in range(args.steps):
+            its, ms, _ = _timed(run, s)
+            ms_all.append(ms)
+        ms = statistics.median(ms_all)
+        ci = sum(c * it for c, it in zip(cells, its))
+        res[name] = {"ms": ms, "solves_per_s": len(items) / (ms / 1e3), "cells_iters_per_s": ci / (ms / 1e3),
+                     "gbs_equiv": 4.0 * sum(c * (it + 2) for c, it in zip(cells, its)) / (ms / 1e3) / 1e9,
+                     "iters_total": int(sum(its))}
+        if b is not None:
+            b.close()
+    best = res.get("batched_tuned", res["batched"])
+    peak, peak_kind = _peaks()
+    line = {"metric": METRIC, "value": best["cells_iters_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"c3_{len(items)}_ragged: batched persistent launch (graph) vs per-instance loop",
+                       "instances": len(items), "cells": int(sum(cells)), "tol": TOL, "eps_rel": 0.05,
+                       "inputs_s": gen_s},
+            "batched_vs_plain": {"solves_per_s_ratio": best["solves_per_s"] / res["plain"]["solves_per_s"],
+                                 **{k: v for k, v in res.items()}},
+            "roofline": {"bound": "hbm", "kernel": "sk_batch", "achieved": best["gbs_equiv"], "peak": peak,
+                         "unit": "GB/s", "frac": best["gbs_equiv"] / peak, "traffic": None, "peak_kind": peak_kind}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_c4(args):
+    """The 400,000 x 4,096 instance (16 km^2, hot spots, capacity q), eps = 0.05 median(C):
+    the log-domain FP32 solver against the stored-kernel solver with K~ in BF16 and FP16."""
+    from paper_1805_01559_gb300 import instances as ins
+    I, J, block = args.c4_rows, 4096, 8192
+    inst = ins.config4_blocked(0, I, J, block)
+    pool = _pool(min(16, os.cpu_count() or 1))
+    import torch
+    from paper_1805_01559_gb300 import binding
+    ctx = binding.Context(0)
+    dev = torch.device("cuda", 0)
+    P = torch.from_numpy(inst.P.astype(np.float32)).to(dev)
+    C = torch.empty((I, J), dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    jobs = [(0, I, J, block, b) for b in range(inst.nblocks)]
+    for b, G in pool.imap_unordered(_gen_c4_block, jobs):
+        r0 = b * block
+        Gd = torch.from_numpy(G).to(dev)
+        R = ctx.build_rates(Gd, P, inst.N0, inst.W_hz)
+        ctx.build_cost(R, inst.mu, C_out=C[r0:r0 + G.shape[0]])
+        del Gd, R
+    pool.close()
+    gen_s = time.perf_counter() - t0
+    med = ctx.median_f32(C.view(-1))
+    eps = 0.05 * med
+    p = torch.from_numpy(inst.lam.astype(np.float32)).to(dev)
+    q = torch.from_numpy(inst.q.astype(np.float32)).to(dev)
+    s = torch.cuda.current_stream()
+    out = {}
+    ref = None
+    for name, fn in (("f32_log", lambda: ctx.solve_cost(C, p, q, eps, tol=TOL, max_iter=MAX_ITER)),
+                     ("bf16_K", lambda: ctx.solve_lowp(C, p, q, eps, tol=TOL, max_iter=MAX_ITER,
+                                                       fmt=binding.OT_KERNEL_BF16)),
+                     ("f16_K", lambda: ctx.solve_lowp(C, p, q, eps, tol=TOL, max_iter=MAX_ITER,
+                                                      fmt=binding.OT_KERNEL_F16))):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        r, ms, _ = _timed(fn, s)
+        if ref is None:
+            ref = r
+        out[name] = {"ms": ms, "iters": r.iters, "absorptions": r.absorptions,
+                     "cells_iters_per_s": I * J * r.iters / (ms / 1e3), "transport_cost": r.transport_cost,
+                     "cost_rel_vs_f32": abs(r.transport_cost - ref.transport_cost) / ref.transport_cost,
+                     "marg_err_row": r.marg_err_row, "marg_err_col": r.marg_err_col, "status": r.status}
+    best = out["bf16_K"]
+    line = {"metric": METRIC, "value": best["cells_iters_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 K~ (FP32 accumulation)", "data": "synthetic",
+            "config": {"workload": f"c4_{I}x{J}: stored-kernel BF16/FP16 vs log-domain FP32",
+                       "I": I, "J": J, "eps": eps, "tol": TOL, "inputs_s": gen_s},
+            "formats": out}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_c5(args):
+    """Serving: 64 cells (I in {5k, 20k, 80k}, J in {128, 512, 1024}), devices moving 1-30 m/s,
+    Poisson arrivals at args.c5_rate req/s for args.c5_seconds s, replayed in real time; each
+    request moves its cell's devices by the time since the cell's previous request and is
+    solved warm (eps fixed per cell at 0.05 median of its first instance)."""
+    from multiprocessing import shared_memory
+    from paper_1805_01559_gb300 import instances as ins
+    shapes = ins.serving_cell_shapes(64)
+    pool = _pool(min(16, os.cpu_count() or 1))
+    import torch
+    from paper_1805_01559_gb300 import binding
+    ctx = binding.Context(0)
+    srv = ctx.server(group_ctas=args.c5_group)
+    t0 = time.perf_counter()
+    ids, resident = [], 0
+    gen = list(pool.imap(_gen_c5, shapes, chunksize=1))
+    pool.close()
+    try:
+        for d in gen:
+            shm = shared_memory.SharedMemory(name=d["shm"])
+            sh = np.ndarray((d["I"], d["J"]), np.float32, buffer=shm.buf)
+            try:
+                cid = srv.add_cell(d["I"], d["J"], 0.0, np.ones(d["J"]), d["lam"], d["q"], ins.MU_PER_BIT,
+                                   ins.noise_power_w(), ins.W_HZ, tol=TOL, max_iter=MAX_ITER, dev_xy=d["dev_xy"],
+                                   dev_v=d["vel"], rrh_xy=d["rrh_xy"], shadow_db=sh, side_m=d["side"], eps_rel=0.05)
+            finally:
+                del sh
+                shm.close()
+                shm.unlink()
+                d["shm"] = None
+            ids.append(cid)
+    finally:
+        for d in gen:  # blocks not uploaded (an error above)
+            if d["shm"]:
+                try:
+                    shared_memory.SharedMemory(name=d["shm"]).unlink()
+                except FileNotFoundError:
+                    pass
+    gen_s = time.perf_counter() - t0
+    t_arr, cells = ins.poisson_arrivals(args.c5_rate, args.c5_seconds, len(ids), seed=0)
+    last = np.zeros(len(ids))
+    results = []
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    start = time.perf_counter()
+    for t, c in zip(t_arr, cells):
+        while time.perf_counter() - start < t:
+            results += srv.poll()
+        dt = float(t - last[c]) if last[c] > 0 else 0.0
+        last[c] = t
+        srv.submit(ids[c], None, dt)
+    results += srv.drain(timeout_s=600)
+    wall = time.perf_counter() - start
+    clk = clocks.stop()
+    lat = np.array([r.latency_us for r in results]) / 1e3
+    ok = [r for r in results if r.status in (0, 1)]
+    t_first = min(r.t_submit_us for r in results)
+    t_last = max(r.t_done_us for r in results)
+    solves_per_s = len(ok) / ((t_last - t_first) / 1e6)
+    its = np.array([r.iters for r in ok])
+    err = np.array([max(r.marg_err_row, r.marg_err_col) for r in ok])
+    cells_map = {cid: shapes[k] for k, cid in enumerate(ids)}
+    ci = sum(cells_map[r.cell][0] * cells_map[r.cell][1] * r.iters for r in ok)
+    st = srv.stats()
+    line = {"metric": "served solves/s", "value": solves_per_s, "unit": "solves/s", "n_gpus": 1, "steps": len(results),
+            "warmup": 0, "ms_per_step": float(np.mean(lat)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"c5_serving: 64 cells, Poisson {args.c5_rate:g} req/s for {args.c5_seconds:g} s",
+                       "offered_per_s": len(t_arr) / args.c5_seconds, "requests": len(t_arr),
+                       "group_ctas": args.c5_group, "kernel": "FP32 log domain (stored-kernel serving not built)",
+                       "resident_bytes": st["resident_bytes"], "launches": st["launches"], "inputs_s": gen_s},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "iters": {"mean": float(its.mean()), "p99": float(np.percentile(its, 99))},
+            "marg_err_max": float(err.max()), "failed": len(results) - len(ok),
+            "cells_iters_per_s": ci / ((t_last - t_first) / 1e6), "wall_s": wall, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    srv.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,9 +626,19 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=12_500)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="only run this many solves of the benchmark instance (for profiler captures)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2: the headline line; c3 batched ragged; c4 stored-kernel precision; c5 serving")
+    ap.add_argument("--c3-instances", type=int, default=256)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--c4-rows", type=int, default=400_000)
+    ap.add_argument("--c5-rate", type=float, default=2000.0)
+    ap.add_argument("--c5-seconds", type=float, default=10.0)
+    ap.add_argument("--c5-group", type=int, default=19)
     args = ap.parse_args()
     if args.profile_solves > 0:
         return run_profile_solve(args)
+    if args.workload != "c2" and args.impl != "reference":
+        return {"c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

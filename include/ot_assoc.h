@@ -376,9 +376,11 @@ typedef struct {
     int64_t I;
     int32_t J;
     int32_t warm_start;  /* != 0: each request starts from the previous request's g */
-    double eps, tol;     /* tol < 0 = 1e-6 */
+    double eps, tol;     /* eps <= 0: eps = eps_rel * median(C) of the cell's first instance
+                            (drifting cells); tol < 0 = 1e-6 */
     int32_t max_iter;    /* <= 0 = 2000 */
     int32_t reserved;
+    double eps_rel;
     double mu, N0, W_hz; /* rates and cost (Sec. II-A, Sec. IV) */
     const float* P;      /* [host] J transmit powers */
     const float* p;      /* [host] I traffic (> 0) */
@@ -426,6 +428,8 @@ ot_status ot_assoc_server_drain(ot_assoc_server* s, double timeout_s);
 ot_status ot_assoc_server_cell_state(const ot_assoc_server* s, int32_t cell, const float** C, double** f,
                                      double** g, double** rrh_load);
 ot_status ot_assoc_server_stats(const ot_assoc_server* s, ot_assoc_server_stats_t* out);
+/* The eps a cell solves with [host]. */
+ot_status ot_assoc_server_cell_eps(const ot_assoc_server* s, int32_t cell, double* eps);
 
 #ifdef __cplusplus
 }

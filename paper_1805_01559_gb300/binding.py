@@ -558,7 +558,8 @@ class ot_assoc_cell_desc(ctypes.Structure):
     _fields_ = [
         ("I", ctypes.c_int64), ("J", ctypes.c_int32), ("warm_start", ctypes.c_int32),
         ("eps", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
-        ("reserved", ctypes.c_int32), ("mu", ctypes.c_double), ("N0", ctypes.c_double), ("W_hz", ctypes.c_double),
+        ("reserved", ctypes.c_int32), ("eps_rel", ctypes.c_double), ("mu", ctypes.c_double),
+        ("N0", ctypes.c_double), ("W_hz", ctypes.c_double),
         ("P", ctypes.c_void_p), ("p", ctypes.c_void_p), ("q", ctypes.c_void_p),
         ("dev_xy", ctypes.c_void_p), ("dev_v", ctypes.c_void_p), ("rrh_xy", ctypes.c_void_p),
         ("shadow_db", ctypes.c_void_p), ("side_m", ctypes.c_double),
@@ -592,11 +593,12 @@ SIGNATURES.update({
     "ot_assoc_server_cell_state": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                                                   ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "ot_assoc_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ot_assoc_server_stats_t)]),
+    "ot_assoc_server_cell_eps": (ctypes.c_int, [_VP, _I32, _PD]),
 })
 if _lib is not None:  # already loaded: register the new entry points
     for _name in ("ot_assoc_server_create", "ot_assoc_server_destroy", "ot_assoc_server_add_cell",
                   "ot_assoc_server_submit", "ot_assoc_server_poll", "ot_assoc_server_drain",
-                  "ot_assoc_server_cell_state", "ot_assoc_server_stats"):
+                  "ot_assoc_server_cell_state", "ot_assoc_server_stats", "ot_assoc_server_cell_eps"):
         _fn = getattr(_lib, _name)
         _fn.restype, _fn.argtypes = SIGNATURES[_name]
 
@@ -633,7 +635,9 @@ class Server:
         self._keep = {}  # host arrays and request gains kept alive
 
     def add_cell(self, I, J, eps, P, p, q, mu, N0, W_hz, tol=1e-6, max_iter=2000, warm_start=True,
-                 dev_xy=None, dev_v=None, rrh_xy=None, shadow_db=None, side_m=0.0) -> int:
+                 dev_xy=None, dev_v=None, rrh_xy=None, shadow_db=None, side_m=0.0, eps_rel=0.0) -> int:
+        """Register a cell; eps <= 0 with eps_rel > 0 (drifting cells) takes eps = eps_rel x
+        median(C) of the first instance."""
         import numpy as np
         arrs = {"P": np.ascontiguousarray(P, np.float32), "p": np.ascontiguousarray(p, np.float32),
                 "q": np.ascontiguousarray(q, np.float32)}
@@ -643,7 +647,7 @@ class Server:
                         shadow_db=np.ascontiguousarray(shadow_db, np.float32))
         d = ot_assoc_cell_desc()
         d.I, d.J, d.warm_start = int(I), int(J), 1 if warm_start else 0
-        d.eps, d.tol, d.max_iter = float(eps), float(tol), int(max_iter)
+        d.eps, d.tol, d.max_iter, d.eps_rel = float(eps), float(tol), int(max_iter), float(eps_rel)
         d.mu, d.N0, d.W_hz = float(mu), float(N0), float(W_hz)
         for k, v in arrs.items():
             setattr(d, k, v.ctypes.data)
@@ -651,6 +655,11 @@ class Server:
         cid = ctypes.c_int32(-1)
         self._ctx._check(self._L.ot_assoc_server_add_cell(self._h, ctypes.byref(d), ctypes.byref(cid)))
         return cid.value
+
+    def cell_eps(self, cell: int) -> float:
+        e = ctypes.c_double(0.0)
+        self._ctx._check(self._L.ot_assoc_server_cell_eps(self._h, int(cell), ctypes.byref(e)))
+        return e.value
 
     def submit(self, cell: int, G: Optional[torch.Tensor] = None, dt: float = 0.0) -> int:
         t = ctypes.c_uint64(0)

@@ -288,7 +288,13 @@ __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg&
                         if (col < J) {
                             Chunk<T>::load(row + col, x[v]);
 #pragma unroll
-                            for (int e = 0; e < N; ++e) ssum = fmaf(x[v][e], Bs[col + e], ssum);
+                            for (int e = 0; e < N; e += 4) {  // beta four at a time (16-byte loads)
+                                const float4 bq = *reinterpret_cast<const float4*>(Bs + col + e);
+                                ssum = fmaf(x[v][e], bq.x, ssum);
+                                ssum = fmaf(x[v][e + 1], bq.y, ssum);
+                                ssum = fmaf(x[v][e + 2], bq.z, ssum);
+                                ssum = fmaf(x[v][e + 3], bq.w, ssum);
+                            }
                         } else {
 #pragma unroll
                             for (int e = 0; e < N; ++e) x[v][e] = 0.f;

@@ -33,11 +33,25 @@ namespace ota {
 static constexpr int SV_CAP = 1024;  // descriptors in the queue ring
 
 // Host-mapped queue (pinned host memory the kernel reads and writes).
+// How a request's cost is rebuilt, by the CTAs that solve it, from their own rows.
+struct SvPrep {
+    const float* G;      // gains [I][ld_g] (caller mode), or nullptr: drifting cell
+    int64_t ld_g;
+    double* dev_xy;      // [I][2] (drift mode)
+    double* dev_v;       // [I][2]
+    const float* rrh_xy; // [J][2]
+    const float* shadow; // [I][J] dB
+    const float* P;      // [J]
+    double dt, side;
+    float N0, W, mu, pad;
+};
+
 struct SvQueue {
     unsigned tail;   // descriptors published (host writes, release)
     unsigned stop;   // host asks idle groups to leave at once
     unsigned pad[30];
     BInst desc[SV_CAP];
+    SvPrep prep[SV_CAP];
     BRes res[SV_CAP];
     unsigned done[SV_CAP];  // sequence number + 1 of the request whose result is in res[]
 };
@@ -45,6 +59,7 @@ struct SvQueue {
 struct SvCtl {  // device memory, zeroed once
     unsigned head;  // descriptors claimed
     int abort;
+    unsigned idle;  // groups of the current launch that found no work (zeroed per launch)
 };
 
 struct ServeParams {
@@ -54,7 +69,7 @@ struct ServeParams {
     const BGroup* groups;
     unsigned* gbar;      // [ngroups]
     int* gcur;           // [ngroups]
-    int gsize;
+    int gsize, ngroups;
     long long idle_polls;
     long long spin;
 };
@@ -68,10 +83,79 @@ __device__ __forceinline__ void st_release_sys_u32(unsigned* p, unsigned v) {
     asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Rebuild the cost of rows [r0, r1) of a request's instance (all threads of the CTA, one warp
+// per row): positions moved by dt (drift mode; FP32 arithmetic, lanes 0 and 1 one axis each)
+// and gains from the path-loss model with the cell's fixed shadowing (in the form
+// 2^(a - (n/2) log2 d^2) on the SFU: a simulation input), or the caller's gains; then the
+// rates with every other RRH interfering (Sec. II-A; the row total of received powers as an
+// FP32 pair) and C = 1 / (mu R).  The first pass leaves the received powers in the cost row,
+// the second turns them into costs.  Invalid rates fail the request.
+__device__ __forceinline__ void sv_rebuild_rows(const SvPrep& Q, float* C, int64_t ldc, int J, int64_t r0, int64_t r1,
+                                                int* status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float inv_ln2 = 1.4426950408889634f;
+    const float l2_10 = 3.3219280948873622f;  // log2(10)
+    const float a0 = -30.0f * 0.1f * l2_10;   // -PL0/10 log2(10), PL0 = 30 dB
+    const float half_n = 0.5f * 3.5f;         // log2 G = a0 + X/10 log2(10) - (n/2) log2 d^2
+    const float side = (float)Q.side, dt = (float)Q.dt;
+    int bad = 0;
+    for (int64_t i = r0 + warp; i < r1; i += nw) {
+        float pos = 0.f;
+        if (!Q.G && lane < 2) {  // lane 0: x, lane 1: y
+            const float x0 = (float)Q.dev_xy[2 * i + lane], v = (float)Q.dev_v[2 * i + lane];
+            const float x1 = fmaf(v, dt, x0);
+            const float per = 2.f * side;
+            float pm = x1 - per * floorf(x1 / per);
+            if (pm > side) pm = per - pm;
+            if (((int)floorf(x1 / side)) & 1) Q.dev_v[2 * i + lane] = -(double)v;
+            Q.dev_xy[2 * i + lane] = (double)pm;
+            pos = pm;
+        }
+        const float x = __shfl_sync(0xffffffffu, pos, 0), y = __shfl_sync(0xffffffffu, pos, 1);
+        float* row = C + i * ldc;
+        float hi = 0.f, lo = 0.f;
+        for (int j = lane; j < J; j += 32) {
+            float v;
+            if (Q.G) {
+                v = Q.P[j] * __ldg(Q.G + i * Q.ld_g + j);
+            } else {
+                const float dx = x - Q.rrh_xy[2 * j], dy = y - Q.rrh_xy[2 * j + 1];
+                const float d2 = fmaxf(fmaf(dx, dx, dy * dy), 100.0f);  // d >= 10 m
+                const float e = fmaf(Q.shadow[i * (int64_t)J + j], 0.1f * l2_10, a0) - half_n * __log2f(d2);
+                v = Q.P[j] * ex2(e);
+            }
+            row[j] = v;
+            float t, e2;
+            two_sum(hi, v, t, e2);
+            hi = t;
+            lo += e2;
+        }
+        warp_sum_pair(hi, lo);
+        __syncwarp();
+        for (int j = lane; j < J; j += 32) {
+            const float pg = row[j];
+            const float interf = ((hi - pg) + lo) + Q.N0;
+            const float R = Q.W * log1pf(__fdividef(pg, interf)) * inv_ln2;
+            const bool ok = R > 0.f && isfinite(R);
+            bad |= !ok;
+            row[j] = ok ? __frcp_rn(Q.mu * R) : INFINITY;
+        }
+    }
+    if (bad) atomicCAS(status, DEV_OK, DEV_EINVAL);
+}
+
+// The same rebuild as a standalone launch over all rows (a cell's first instance, dt = 0).
+__global__ void __launch_bounds__(256) sv_rebuild_all(SvPrep Q, float* C, int64_t ldc, int64_t I, int J, int* status) {
+    const int64_t rows_per_block = 8 * ((I + 8LL * gridDim.x - 1) / (8LL * gridDim.x));
+    const int64_t r0 = min(I, (int64_t)blockIdx.x * rows_per_block), r1 = min(I, r0 + rows_per_block);
+    sv_rebuild_rows(Q, C, ldc, J, r0, r1, status);
+}
+
 __global__ void __launch_bounds__(BT_NT, 1) sk_serve(ServeParams S) {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ SkShared sh;
     __shared__ __align__(16) BInst s_inst;
+    __shared__ __align__(16) SvPrep s_prep;
     __shared__ unsigned s_gen;
     __shared__ int s_idx, s_nbar;
     const int gi = blockIdx.x / S.gsize, rank = blockIdx.x % S.gsize;
@@ -84,9 +168,12 @@ __global__ void __launch_bounds__(BT_NT, 1) sk_serve(ServeParams S) {
     __syncthreads();
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) {
-            // claim the next published request, or give up after the idle limit
+            // claim the next published request.  A group that found nothing for idle_polls
+            // polls reports itself idle and keeps polling; when every group of the launch is
+            // idle they all leave (the host relaunches on new work).  At most `spin` polls.
             int idx = -1;
             long long n = 0;
+            bool counted = false;
             for (;;) {
                 if (ld_acquire_sys_u32(&S.q->stop)) break;
                 const unsigned t = ld_acquire_sys_u32(&S.q->tail);
@@ -94,12 +181,19 @@ __global__ void __launch_bounds__(BT_NT, 1) sk_serve(ServeParams S) {
                 if (h < t) {
                     if (atomicCAS(&S.ctl->head, h, h + 1) == h) {
                         idx = (int)h;
+                        if (counted) atomicSub(&S.ctl->idle, 1u);
                         break;
                     }
                     continue;
                 }
-                if (++n > S.idle_polls) break;
-                __nanosleep(256);
+                ++n;
+                if (!counted && n > S.idle_polls) {
+                    atomicAdd(&S.ctl->idle, 1u);
+                    counted = true;
+                }
+                if (counted && *(volatile unsigned*)&S.ctl->idle >= (unsigned)S.ngroups) break;
+                if (n > S.spin) break;
+                __nanosleep(n < 4096 ? 256 : 2048);
             }
             if (idx >= 0) {
                 BRes* r = S.dres + (idx % SV_CAP);
@@ -114,75 +208,29 @@ __global__ void __launch_bounds__(BT_NT, 1) sk_serve(ServeParams S) {
         const int idx = s_idx;
         if (idx < 0) return;
         const int slot = idx % SV_CAP;
-        {  // the descriptor into shared memory (read once from host memory)
+        {  // the descriptors into shared memory (read once from host memory)
             const unsigned* src = reinterpret_cast<const unsigned*>(&S.q->desc[slot]);
             unsigned* dst = reinterpret_cast<unsigned*>(&s_inst);
             for (int k = threadIdx.x; k < (int)(sizeof(BInst) / 4); k += blockDim.x) dst[k] = src[k];
+            const unsigned* src2 = reinterpret_cast<const unsigned*>(&S.q->prep[slot]);
+            unsigned* dst2 = reinterpret_cast<unsigned*>(&s_prep);
+            for (int k = threadIdx.x; k < (int)(sizeof(SvPrep) / 4); k += blockDim.x) dst2[k] = src2[k];
         }
         __syncthreads();
         BRes* out = S.dres + slot;
+        {  // this CTA's rows of the new cost, before its bulk copies read them
+            int64_t r0, r1;
+            cta_rows(s_inst.P.I, s_inst.S.rows_per_stage, s_inst.P.V, rank, S.gsize, &r0, &r1);
+            sv_rebuild_rows(s_prep, const_cast<float*>(s_inst.P.C), s_inst.P.ld, s_inst.P.J, r0, r1, &out->status);
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            __syncthreads();
+        }
         if (!bt_run(s_inst, out, &S.ctl->abort, S.spin, grp, rank, S.gsize, gbar, &s_gen, &s_nbar, &sh, dyn))
             return;
         if (rank == 0 && threadIdx.x == 0) {
             S.q->res[slot] = *out;
             __threadfence_system();
             st_release_sys_u32(&S.q->done[slot], (unsigned)idx + 1u);
-        }
-    }
-}
-
-// Cost of a drifting cell's new time instance: devices move by v dt (reflecting at the
-// square's walls), gains from the path-loss model with the cell's fixed shadowing, rates
-// with every other RRH interfering (Sec. II-A), C = 1 / (mu R).  One warp per device.
-__global__ void __launch_bounds__(256) serve_channel(double* dev_xy, double* dev_v, const float* __restrict__ rrh_xy,
-                                                     const float* __restrict__ shadow_db, int64_t I, int J,
-                                                     double side, double dt, const float* __restrict__ P,
-                                                     float N0, float W, float mu, float pl0_db, float pl_exp,
-                                                     float d_min, float* C, int64_t ldc) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const float inv_ln2 = 1.4426950408889634f;
-    for (int64_t i = w0; i < I; i += nw) {
-        double xy[2];
-        if (lane == 0) {
-            for (int ax = 0; ax < 2; ++ax) {
-                const double x0 = dev_xy[2 * i + ax], v = dev_v[2 * i + ax];
-                const double x1 = x0 + v * dt;
-                double pm = fmod(x1, 2.0 * side);
-                if (pm < 0.0) pm += 2.0 * side;
-                if (pm > side) pm = 2.0 * side - pm;
-                const long long k = (long long)floor(x1 / side);
-                if (k & 1LL) dev_v[2 * i + ax] = -v;
-                dev_xy[2 * i + ax] = pm;
-                xy[ax] = pm;
-            }
-        }
-        const float x = (float)__shfl_sync(0xffffffffu, xy[0], 0), y = (float)__shfl_sync(0xffffffffu, xy[1], 0);
-        const float* sh = shadow_db + i * (int64_t)J;
-        // received powers P_j G_ij: the row total first (pairs of FP32), then the rates
-        float tot_hi = 0.f, tot_lo = 0.f;
-        for (int j = lane; j < J; j += 32) {
-            const float dx = x - rrh_xy[2 * j], dy = y - rrh_xy[2 * j + 1];
-            const float d = fmaxf(sqrtf(dx * dx + dy * dy), d_min);
-            const float pl = pl0_db + 10.f * pl_exp * log10f(d) - sh[j];
-            const float pg = P[j] * exp10f(-0.1f * pl);
-            float s, e;
-            two_sum(tot_hi, pg, s, e);
-            tot_hi = s;
-            tot_lo += e;
-        }
-        float tot = tot_hi + tot_lo;
-        tot = warp_sum(tot);
-        float* row = C + i * ldc;
-        for (int j = lane; j < J; j += 32) {
-            const float dx = x - rrh_xy[2 * j], dy = y - rrh_xy[2 * j + 1];
-            const float d = fmaxf(sqrtf(dx * dx + dy * dy), d_min);
-            const float pl = pl0_db + 10.f * pl_exp * log10f(d) - sh[j];
-            const float pg = P[j] * exp10f(-0.1f * pl);
-            const float sinr = pg / ((tot - pg) + N0);
-            const float R = W * log1pf(sinr) * inv_ln2;
-            row[j] = 1.0f / (mu * R);
         }
     }
 }
@@ -220,8 +268,6 @@ struct Cell {
     double* dev_v = nullptr;
     float* rrh_xy = nullptr;
     float* shadow = nullptr;
-    float* R = nullptr;  // rates scratch when the caller gives gains
-    unsigned long long* bad = nullptr;  // invalid rates of the last cost rebuild
     std::vector<void*> allocs;
     size_t bytes = 0;
     // scheduling
@@ -237,7 +283,6 @@ struct Request {
     double dt;
     double t_submit, t_start;
     unsigned seq;
-    cudaEvent_t prep_done = nullptr;
 };
 
 }  // namespace
@@ -251,15 +296,13 @@ struct ot_assoc_server {
     void* dmem = nullptr;
     size_t dbytes = 0;
     ota::ServeParams params{};
-    cudaStream_t prep_stream = nullptr, run_stream = nullptr;
+    cudaStream_t run_stream = nullptr;
     cudaEvent_t run_done = nullptr;
     bool running = false;
     size_t smem = 0;
     std::vector<Cell> cells;
     std::deque<Request> waiting;     // submitted, cell busy or not yet started
-    std::vector<Request> prepping;   // cost rebuild enqueued
     std::vector<Request> inflight;   // published to the kernel
-    std::vector<cudaEvent_t> free_events;
     uint64_t next_ticket = 1;
     unsigned published = 0;
     size_t resident = 0;
@@ -301,8 +344,9 @@ static ot_status sv_launch(ot_assoc_server* s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // group barrier counters restart with every launch
+    // group barrier counters and the idle count restart with every launch
     cudaError_t e = cudaMemsetAsync(s->params.gbar, 0, sizeof(unsigned) * s->ngroups, s->run_stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&s->params.ctl->idle, 0, sizeof(unsigned), s->run_stream);
     if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, sk_serve, s->params);
     if (e == cudaSuccess) e = cudaEventRecord(s->run_done, s->run_stream);
     if (e != cudaSuccess) return cuda_error(ctx, e, "server launch");
@@ -312,39 +356,7 @@ static ot_status sv_launch(ot_assoc_server* s) {
     return OT_OK;
 }
 
-// Enqueue the cost rebuild of a request's time instance on the prep stream.
-static ot_status sv_prep(ot_assoc_server* s, Request& r) {
-    ot_assoc_ctx* ctx = s->ctx;
-    Cell& c = s->cells[r.cell];
-    ot_status st = OT_OK;
-    cudaError_t e0 = cudaMemsetAsync(c.bad, 0, sizeof(unsigned long long), s->prep_stream);
-    if (e0 != cudaSuccess) return cuda_error(ctx, e0, "memset");
-    if (r.G) {
-        st = launch_rates(ctx, r.G, r.ld_g, c.P, c.I, c.J, c.N0, c.W, c.R, c.ldc, s->prep_stream);
-        if (st) return st;
-        st = launch_cost(ctx, c.R, c.ldc, c.I, c.J, c.mu, c.C, c.ldc, true, c.bad, s->prep_stream);
-        if (st) return st;
-    } else {
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((c.I + 7) / 8, 8LL * ctx->num_sms));
-        serve_channel<<<grid, 256, 0, s->prep_stream>>>(c.dev_xy, c.dev_v, c.rrh_xy, c.shadow, c.I, c.J, c.side, r.dt,
-                                                       c.P, (float)c.N0, (float)c.W, (float)c.mu, 30.0f, 3.5f, 10.0f,
-                                                       c.C, c.ldc);
-        ctx->launches += 1;
-    }
-    if (s->free_events.empty()) {
-        cudaEvent_t ev;
-        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_error(ctx, e, "event");
-        s->free_events.push_back(ev);
-    }
-    r.prep_done = s->free_events.back();
-    s->free_events.pop_back();
-    cudaError_t e = cudaEventRecord(r.prep_done, s->prep_stream);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "event record");
-    return OT_OK;
-}
-
-// Publish a prepared request to the kernel's queue.
+// Publish a request to the kernel's queue (its cell is idle).
 static ot_status sv_publish(ot_assoc_server* s, Request& r) {
     Cell& c = s->cells[r.cell];
     const unsigned seq = s->published;
@@ -366,12 +378,26 @@ static ot_status sv_publish(ot_assoc_server* s, Request& r) {
     a.g = c.g;
     a.rrh_load = c.rho;
     fill_values(&d, a);
-    d.P.input_bad = c.bad;  // invalid rates in the cost rebuild fail the request
     d.vpt = vpt_for(c.J);
     size_t sm = 0;
     if (!plan_stream(c.I, d.P.Jp, c.ldc, s->gsize, 24576, &d.S, &sm, &d.P.V))
         return set_error(s->ctx, OT_EUNSUPPORTED, "cell does not fit the server's groups");
+    SvPrep pr;
+    std::memset(&pr, 0, sizeof(pr));
+    pr.G = r.G;
+    pr.ld_g = r.ld_g;
+    pr.dev_xy = c.dev_xy;
+    pr.dev_v = c.dev_v;
+    pr.rrh_xy = c.rrh_xy;
+    pr.shadow = c.shadow;
+    pr.P = c.P;
+    pr.dt = r.dt;
+    pr.side = c.side;
+    pr.N0 = (float)c.N0;
+    pr.W = (float)c.W;
+    pr.mu = (float)c.mu;
     s->q_host->desc[slot] = d;
+    s->q_host->prep[slot] = pr;
     s->q_host->done[slot] = 0;
     std::atomic_thread_fence(std::memory_order_release);
     __atomic_store_n(&s->q_host->tail, seq + 1u, __ATOMIC_RELEASE);
@@ -383,32 +409,16 @@ static ot_status sv_publish(ot_assoc_server* s, Request& r) {
 
 static ot_status sv_progress(ot_assoc_server* s) {
     ot_assoc_ctx* ctx = s->ctx;
-    // 1. start the cost rebuild of waiting requests whose cell is idle (in submit order)
+    // 1. publish waiting requests whose cell is idle (in submission order)
     for (auto it = s->waiting.begin(); it != s->waiting.end();) {
         Cell& c = s->cells[it->cell];
-        if (c.busy || (int)(s->prepping.size() + s->inflight.size()) >= SV_CAP / 2) {
+        if (c.busy || (int)s->inflight.size() >= SV_CAP / 2) {
             ++it;
             continue;
         }
         c.busy = true;
         Request r = *it;
         it = s->waiting.erase(it);
-        ot_status st = sv_prep(s, r);
-        if (st) return st;
-        s->prepping.push_back(r);
-    }
-    // 2. publish the requests whose cost is ready
-    for (size_t k = 0; k < s->prepping.size();) {
-        cudaError_t e = cudaEventQuery(s->prepping[k].prep_done);
-        if (e == cudaErrorNotReady) {
-            ++k;
-            continue;
-        }
-        if (e != cudaSuccess) return cuda_error(ctx, e, "cost rebuild");
-        Request r = s->prepping[k];
-        s->free_events.push_back(r.prep_done);
-        r.prep_done = nullptr;
-        s->prepping.erase(s->prepping.begin() + k);
         ot_status st = sv_publish(s, r);
         if (st) return st;
         s->inflight.push_back(r);
@@ -504,7 +514,6 @@ ot_status ot_assoc_server_create(ot_assoc_ctx* ctx, const ot_assoc_server_config
     if (e == cudaSuccess) e = cudaMemset(s->dmem, 0, o_scr);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->q_host, sizeof(SvQueue), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&s->q_dev, s->q_host, 0);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->prep_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->run_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->run_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -548,6 +557,7 @@ ot_status ot_assoc_server_create(ot_assoc_ctx* ctx, const ot_assoc_server_config
     P.gbar = (unsigned*)(base + o_gbar);
     P.gcur = (int*)(base + o_gcur);
     P.gsize = s->gsize;
+    P.ngroups = s->ngroups;
     P.idle_polls = (long long)(idle / 0.3);  // a poll sleeps about 0.3 us
     P.spin = ctx->spin_limit;
     s->smem = SMEM_BUDGET;
@@ -573,14 +583,9 @@ void ot_assoc_server_destroy(ot_assoc_server* s) {
     DeviceGuardLite guard(s->ctx->device);
     if (s->q_host) __atomic_store_n(&s->q_host->stop, 1u, __ATOMIC_RELEASE);
     if (s->run_stream) cudaStreamSynchronize(s->run_stream);
-    if (s->prep_stream) cudaStreamSynchronize(s->prep_stream);
     for (auto& c : s->cells) sv_free_cell(s, c);
-    for (auto& r : s->prepping)
-        if (r.prep_done) cudaEventDestroy(r.prep_done);
-    for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
     if (s->run_done) cudaEventDestroy(s->run_done);
     if (s->run_stream) cudaStreamDestroy(s->run_stream);
-    if (s->prep_stream) cudaStreamDestroy(s->prep_stream);
     if (s->q_host) cudaFreeHost(s->q_host);
     if (s->dmem) cudaFree(s->dmem);
     delete s;
@@ -593,8 +598,10 @@ ot_status ot_assoc_server_add_cell(ot_assoc_server* s, const ot_assoc_cell_desc*
     if (d->I <= 0 || d->J <= 0) return set_error(ctx, OT_EINVAL, "I and J must be positive");
     const int maxJ = s->cfg.max_J > 0 ? s->cfg.max_J : 1024;
     if (d->J > maxJ) return set_error(ctx, OT_EUNSUPPORTED, "J=%d above the server's max_J=%d", d->J, maxJ);
-    if (!(d->eps > 0.0) || !(d->mu > 0.0) || !(d->W_hz > 0.0) || !(d->N0 > 0.0))
-        return set_error(ctx, OT_EINVAL, "eps, mu, W and N0 must be > 0");
+    if (!(d->mu > 0.0) || !(d->W_hz > 0.0) || !(d->N0 > 0.0))
+        return set_error(ctx, OT_EINVAL, "mu, W and N0 must be > 0");
+    if (!(d->eps > 0.0) && !(d->eps_rel > 0.0 && d->dev_xy))
+        return set_error(ctx, OT_EINVAL, "eps must be > 0 (or eps_rel > 0 for a drifting cell)");
     if (!d->P || !d->p || !d->q) return set_error(ctx, OT_EINVAL, "P, p and q are required");
     const bool drift = d->dev_xy != nullptr;
     if (drift && (!d->dev_v || !d->rrh_xy || !d->shadow_db || !(d->side_m > 0.0)))
@@ -640,21 +647,17 @@ ot_status ot_assoc_server_add_cell(ot_assoc_server* s, const ot_assoc_cell_desc*
     SV_ALLOC(f, double, I);
     SV_ALLOC(g, double, ldc);
     SV_ALLOC(rho, double, ldc);
-    SV_ALLOC(bad, unsigned long long, 1);
     if (drift) {
         SV_ALLOC(dev_xy, double, 2 * I);
         SV_ALLOC(dev_v, double, 2 * I);
         SV_ALLOC(rrh_xy, float, 2 * J);
         SV_ALLOC(shadow, float, I * J);
-    } else {
-        SV_ALLOC(R, float, I * ldc);
     }
 #undef SV_ALLOC
     cudaError_t e = cudaMemcpy(c.p, d->p, sizeof(float) * I, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c.q, d->q, sizeof(float) * J, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c.P, d->P, sizeof(float) * J, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c.g, 0, sizeof(double) * ldc);
-    if (e == cudaSuccess) e = cudaMemset(c.bad, 0, sizeof(unsigned long long));
     if (drift) {
         if (e == cudaSuccess) e = cudaMemcpy(c.dev_xy, d->dev_xy, sizeof(double) * 2 * I, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(c.dev_v, d->dev_v, sizeof(double) * 2 * I, cudaMemcpyHostToDevice);
@@ -664,6 +667,57 @@ ot_status ot_assoc_server_add_cell(ot_assoc_server* s, const ot_assoc_cell_desc*
     if (e != cudaSuccess) {
         sv_free_cell(s, c);
         return cuda_error(ctx, e, "cell upload");
+    }
+    if (!(c.eps > 0.0)) {  // eps = eps_rel * median(C) of the first instance (built here, dt = 0)
+        SvPrep pr;
+        std::memset(&pr, 0, sizeof(pr));
+        pr.dev_xy = c.dev_xy;
+        pr.dev_v = c.dev_v;
+        pr.rrh_xy = c.rrh_xy;
+        pr.shadow = c.shadow;
+        pr.P = c.P;
+        pr.side = c.side;
+        pr.N0 = (float)c.N0;
+        pr.W = (float)c.W;
+        pr.mu = (float)c.mu;
+        int* dstat = nullptr;
+        double* dmed = nullptr;
+        st = OT_OK;
+        char* tmp = (char*)scratch(ctx, SLOT_MISC, 256, &st);
+        if (st) {
+            sv_free_cell(s, c);
+            return st;
+        }
+        dstat = (int*)tmp;
+        dmed = (double*)(tmp + 64);
+        e = cudaMemset(dstat, 0, sizeof(int));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((c.I + 63) / 64, 4LL * ctx->num_sms));
+        if (e == cudaSuccess) {
+            sv_rebuild_all<<<grid, 256, 0, s->run_stream>>>(pr, c.C, c.ldc, c.I, c.J, dstat);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            st = launch_median(ctx, c.C, c.I, c.J, c.ldc, dmed, s->run_stream);
+            if (st) {
+                sv_free_cell(s, c);
+                return st;
+            }
+        }
+        double med = 0.0;
+        int hs = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&med, dmed, sizeof(double), cudaMemcpyDeviceToHost, s->run_stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, dstat, sizeof(int), cudaMemcpyDeviceToHost, s->run_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->run_stream);
+        if (e != cudaSuccess) {
+            sv_free_cell(s, c);
+            return cuda_error(ctx, e, "first instance");
+        }
+        if (hs != DEV_OK || !(med > 0.0) || !std::isfinite(med)) {
+            sv_free_cell(s, c);
+            return set_error(ctx, OT_EINVAL, "the cell's first instance has invalid rates");
+        }
+        c.eps = d->eps_rel * med;
+        ctx->launches += 1;
     }
     *cell_id = (int32_t)s->cells.size();
     s->cells.push_back(c);
@@ -716,7 +770,7 @@ ot_status ot_assoc_server_drain(ot_assoc_server* s, double timeout_s) {
     if (!s) return OT_EINVAL;
     DeviceGuardLite guard(s->ctx->device);
     const double t_end = now_us() + 1e6 * (timeout_s > 0 ? timeout_s : 60.0);
-    while (!s->waiting.empty() || !s->prepping.empty() || !s->inflight.empty()) {
+    while (!s->waiting.empty() || !s->inflight.empty()) {
         ot_status st = sv_progress(s);
         if (st) return st;
         if (now_us() > t_end) return set_error(s->ctx, OT_ETIMEOUT, "drain: requests still pending");
@@ -735,6 +789,12 @@ ot_status ot_assoc_server_cell_state(const ot_assoc_server* s, int32_t cell, con
     return OT_OK;
 }
 
+ot_status ot_assoc_server_cell_eps(const ot_assoc_server* s, int32_t cell, double* eps) {
+    if (!s || !eps || cell < 0 || cell >= (int32_t)s->cells.size()) return OT_EINVAL;
+    *eps = s->cells[cell].eps;
+    return OT_OK;
+}
+
 ot_status ot_assoc_server_stats(const ot_assoc_server* s, ot_assoc_server_stats_t* out) {
     if (!s || !out) return OT_EINVAL;
     out->resident_bytes = s->resident;
@@ -742,7 +802,7 @@ ot_status ot_assoc_server_stats(const ot_assoc_server* s, ot_assoc_server_stats_
     out->groups = s->ngroups;
     out->group_ctas = s->gsize;
     out->waiting = (int32_t)s->waiting.size();
-    out->inflight = (int32_t)(s->prepping.size() + s->inflight.size());
+    out->inflight = (int32_t)s->inflight.size();
     out->launches = s->launches;
     return OT_OK;
 }

@@ -297,3 +297,50 @@ def poisson_arrivals(rate_hz: float, duration_s: float, n_cells: int, seed: int 
     t = np.sort(rng.uniform(0.0, duration_s, size=n))
     cells = rng.integers(0, n_cells, size=n)
     return t, cells
+
+
+# ----------------------------------------------------------------------------------------------
+# Large instances in row blocks (each block's shadowing from its own seed), so that the gains
+# can be drawn in parallel and streamed to the device block by block.
+# ----------------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class BlockedInstance:
+    """An instance whose gains are produced block by block (gains_block)."""
+    name: str
+    I: int
+    J: int
+    side: float
+    seed: int
+    block: int
+    rrh_xy: np.ndarray
+    dev_xy: np.ndarray
+    P: np.ndarray
+    N0: float
+    W_hz: float
+    mu: float
+    lam: np.ndarray
+    q: np.ndarray
+
+    @property
+    def nblocks(self) -> int:
+        return (self.I + self.block - 1) // self.block
+
+    def gains_block(self, b: int, dtype=np.float32) -> np.ndarray:
+        r0, r1 = b * self.block, min(self.I, (b + 1) * self.block)
+        rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([self.seed, 7, b])))
+        sh = shadowing_db(r1 - r0, self.J, rng)
+        return path_gains(self.dev_xy[r0:r1], self.rrh_xy, sh, dtype=dtype)
+
+
+def config4_blocked(seed: int = 0, I: int = 400_000, J: int = 4096, block: int = 8192) -> BlockedInstance:
+    """The 400,000 x 4,096 configuration (16 km^2, hot spots, capacity q) in row blocks."""
+    root = np.random.SeedSequence(seed)
+    s_rrh, s_dev, _, s_lam, s_q = [np.random.Generator(np.random.PCG64(s)) for s in root.spawn(5)]
+    side = 4000.0
+    rrh = rrh_jittered_grid(J, side, s_rrh)
+    dev = devices_hotspot(I, side, s_dev)
+    lam = traffic_lognormal(I, 1.5, s_lam)
+    q = capacity_marginal(J, lam.sum(), s_q)
+    return BlockedInstance(name=f"c4_{I}x{J}", I=I, J=J, side=side, seed=seed, block=block, rrh_xy=rrh,
+                           dev_xy=dev, P=np.full(J, P_TX_W), N0=noise_power_w(), W_hz=W_HZ, mu=MU_PER_BIT,
+                           lam=lam, q=q)
