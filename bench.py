@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -109,6 +110,44 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def reduce_ranks(dist, dev, ms: float, work: float):
+    """Whole-job figures of N replicas: the slowest rank's time and the work of all ranks."""
+    import torch
+    t = torch.tensor([float(ms)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(work)], device=dev, dtype=torch.float64)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
+# Solver sources whose change invalidates a stored DRAM-traffic figure of sk_solve.
+SOLVER_SOURCES = ("sk_core.cuh", "k_sinkhorn.cu", "ot_common.cuh")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "sk_solve_c2_50000x800.md")
+
+
+def solver_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in SOLVER_SOURCES:
+        with open(os.path.join(ROOT, "paper_1805_01559_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic():
+    """DRAM bytes per sk_solve launch from the committed ncu summary, or None when the summary
+    is missing or was taken on other solver sources than the ones built now."""
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    m_t = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", text, re.M)
+    m_h = re.search(r"^solver_source_sha256:\s*([0-9a-f]+)", text, re.M)
+    if not m_t or not m_h or m_h.group(1) != solver_source_hash():
+        return None
+    return float(m_t.group(1))
 
 
 def make_inputs():
@@ -250,12 +289,7 @@ def run_gpu(args):
     clk = clocks.stop()
     if dist:
         dist.barrier()
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        c = torch.tensor([float(cells)], device=dev, dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        cells = float(c.item())
+        ms, cells = reduce_ranks(dist, dev, ms, cells)
     value = cells / (ms / 1e3)
 
     # e2e: the same step through the public API with host buffers, copies inside the timed region.
@@ -278,24 +312,13 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = ev0.elapsed_time(ev1)
     if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-        c = torch.tensor([float(e2e_cells)], device=dev, dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        e2e_cells = float(c.item())
+        e2e_ms, e2e_cells = reduce_ranks(dist, dev, e2e_ms, e2e_cells)
     h2d = G_h.numel() * 4 + P_h.numel() * 4 + lam_h.numel() * 4 + q_h.numel() * 4
     d2h = sum(x.numel() * 8 for x in f_h) + sum(x.numel() * 8 for x in g_h)
 
     peak, peak_kind = _peaks()
     achieved = (sum(loop_bytes) / 1e9) / (sum(loop_ms) / 1e3) if loop_ms else None
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "sk_loop_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("traffic_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = stored_traffic()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -311,6 +334,7 @@ def run_gpu(args):
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "bytes_per_cell_iter": 4, "reads_of_C_per_launch": "iters + 2",
+                         "alg_bytes_per_launch": (sum(loop_bytes) / len(loop_bytes)) if loop_bytes else None,
                          "launches_timed": len(loop_ms)},
             "e2e": {"value": e2e_cells / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -328,7 +352,8 @@ def run_gpu(args):
 
 def run_profile_solve(args):
     """Driver for ncu captures of the solver: build the 50,000 x 800 instance, then
-    `--profile-solves` solves at eps = 0.1 median(C) (capture the last with -s/-c)."""
+    `--profile-solves` rounds of the step's three solves (eps = 0.1, 0.03, 0.01 median(C));
+    capture the last round's three sk_solve launches with -s/-c."""
     import torch
 
     from paper_1805_01559_gb300 import binding
@@ -341,11 +366,13 @@ def run_profile_solve(args):
     ctx = binding.Context(0)
     R = ctx.build_rates(G, P, inst.N0, inst.W_hz)
     C, med = ctx.build_cost(R, inst.mu, eps_rel=1.0)
+    its = []
     for _ in range(args.profile_solves):
-        res = ctx.solve_cost(C, lam, q, 0.1 * med, tol=TOL, max_iter=MAX_ITER)
+        its = [ctx.solve_cost(C, lam, q, er * med, tol=TOL, max_iter=MAX_ITER).iters for er in EPS_REL]
     torch.cuda.synchronize()
-    print(json.dumps({"profile_solve": "c2_50000x800 eps=0.1*median", "iters": res.iters,
-                      "cost": res.transport_cost}))
+    print(json.dumps({"profile_solve": "c2_50000x800 eps=(0.1,0.03,0.01)*median", "iters": its,
+                      "alg_bytes_per_launch": 4.0 * inst.I * inst.J * (sum(its) / len(its) + 2),
+                      "solver_source_sha256": solver_source_hash()}))
     ctx.close()
     return 0
 
@@ -625,7 +652,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=12_500)
     ap.add_argument("--profile-solves", type=int, default=0,
-                    help="only run this many solves of the benchmark instance (for profiler captures)")
+                    help="only run this many rounds of the three solves of one step (for profiler captures)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: the headline line; c3 batched ragged; c4 stored-kernel precision; c5 serving")
     ap.add_argument("--c3-instances", type=int, default=256)
