@@ -53,11 +53,14 @@ def _load():
         lib.oracle_finalize.argtypes = [d, d, d, d, d, i64, i64, ctypes.c_double, d, d, d, d]
         lib.oracle_maxsinr.argtypes = [d, d, d, i64, i64, pi32, d, d]
         lib.oracle_adaptive.argtypes = [d, d, i64, i64, ctypes.c_double, ctypes.c_double, i32, i32,
-                                        ctypes.c_double, d, d, d, d]
+                                        ctypes.c_double, d, d, d, d, pi32, d]
+        lib.oracle_completion.argtypes = [d, d, d, i64, i64, d, d]
+        lib.oracle_euclid_cost.argtypes = [d, d, i64, i64, d]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         for name in ("oracle_rates", "oracle_cost", "oracle_median", "oracle_sinkhorn",
-                     "oracle_plan", "oracle_finalize", "oracle_maxsinr", "oracle_adaptive"):
+                     "oracle_plan", "oracle_finalize", "oracle_maxsinr", "oracle_adaptive",
+                     "oracle_completion", "oracle_euclid_cost"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -165,13 +168,41 @@ def maxsinr(R, C, lam):
 
 def adaptive(C, lam, eps: float, tol: float, max_iter: int, outer: int, delta: float):
     """Algorithm 2: (f, g, q used by the last solve, per-step max load)."""
+    f, g, q, ml, _, _ = adaptive_trace(C, lam, eps, tol, max_iter, outer, delta)
+    return f, g, q, ml
+
+
+def adaptive_trace(C, lam, eps: float, tol: float, max_iter: int, outer: int, delta: float):
+    """Algorithm 2 with its trace: (f, g, q, per-step max load, per-step j*, per-step loads (outer x J))."""
     C, lam = _f64(C), _f64(lam)
     I, J = C.shape
     f = np.empty(I)
     g = np.empty(J)
     q = np.empty(J)
     ml = np.empty(outer)
+    js = np.empty(outer, dtype=np.int32)
+    rho = np.empty((outer, J))
     _check(_load().oracle_adaptive(_dp(C), _dp(lam), I, J, float(eps), float(tol), int(max_iter),
-                                   int(outer), float(delta), _dp(f), _dp(g), _dp(q), _dp(ml)),
+                                   int(outer), float(delta), _dp(f), _dp(g), _dp(q), _dp(ml),
+                                   js.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(rho)),
            "adaptive")
-    return f, g, q, ml
+    return f, g, q, ml, js, rho
+
+
+def completion_time(C, x, lam):
+    """Average job completion time of the mass plan x under load costs C, Sec. II-B: (T, rho)."""
+    C, x, lam = _f64(C), _f64(x), _f64(lam)
+    I, J = C.shape
+    T = np.empty(1)
+    rho = np.empty(J)
+    _check(_load().oracle_completion(_dp(C), _dp(x), _dp(lam), I, J, _dp(T), _dp(rho)), "completion")
+    return float(T[0]), rho
+
+
+def euclid_cost(dev_xy, rrh_xy) -> np.ndarray:
+    """C_ij = ||x_i - x_j||, Sec. IV choice (i)."""
+    d, r = _f64(dev_xy), _f64(rrh_xy)
+    I, J = d.shape[0], r.shape[0]
+    C = np.empty((I, J))
+    _check(_load().oracle_euclid_cost(_dp(d), _dp(r), I, J, _dp(C)), "euclid_cost")
+    return C

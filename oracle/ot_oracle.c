@@ -25,6 +25,8 @@
  *   oracle_finalize   pinned (marginals of closed-form plans)
  *   oracle_maxsinr    pinned (brute-force argmax, Lemma 1)
  *   oracle_adaptive   pinned (one outer step by hand, mass conservation)
+ *   oracle_completion pinned (hand-worked two-device cases, overload -> inf)
+ *   oracle_euclid_cost pinned (3-4-5 triangles, symmetry)
  */
 #include <math.h>
 #include <stdint.h>
@@ -368,12 +370,14 @@ int oracle_maxsinr(const double* R, const double* C, const double* lam, int64_t 
  * outer loop: it runs `outer` steps and returns the plan of the last solve
  * together with the q that solve used (the update after it is not applied).
  * A q_j* that delta would drive to zero or below moves half of itself instead,
- * so every marginal stays positive.  The per-step maximum load is written to
- * maxload_out (outer entries) when given.
+ * so every marginal stays positive.  Optional traces (NULL = not wanted): the
+ * per-step maximum load (outer entries), the chosen RRH j* per step (outer
+ * entries) and every step's loads rho (outer x J).
  */
 int oracle_adaptive(const double* C, const double* lam, int64_t I, int64_t J, double eps,
                     double tol, int32_t max_iter, int32_t outer, double delta, double* f,
-                    double* g, double* q_out, double* maxload_out) {
+                    double* g, double* q_out, double* maxload_out, int32_t* jstar_out,
+                    double* rho_out) {
     if (I <= 0 || J <= 1 || outer < 1 || !(delta >= 0.0)) return ORC_EINVAL;
     double total = 0.0;
     for (int64_t i = 0; i < I; ++i) total += lam[i];
@@ -395,6 +399,8 @@ int oracle_adaptive(const double* C, const double* lam, int64_t I, int64_t J, do
         for (int64_t j = 1; j < J; ++j)
             if (rho[j] > rho[js]) js = j;
         if (maxload_out) maxload_out[s] = rho[js];
+        if (jstar_out) jstar_out[s] = (int32_t)js;
+        if (rho_out) memcpy(rho_out + (int64_t)s * J, rho, (size_t)J * sizeof(double));
         if (s == outer - 1) break;
         double d = delta < q[js] ? delta : 0.5 * q[js];
         for (int64_t j = 0; j < J; ++j)
@@ -403,4 +409,60 @@ int oracle_adaptive(const double* C, const double* lam, int64_t I, int64_t J, do
     free(rho);
     free(gw);
     return rc;
+}
+
+/*
+ * Average job completion time of an association, Sec. II-B.
+ * x is a transport plan in mass units (I x J, x_ij = lambda_i pi_ij with pi_ij the
+ * fraction of time device i uses RRH j), C the load cost C_ij = 1/(mu R_ij).
+ *   rho_j = sum_i C_ij x_ij                   (RRH load, Sec. II-B with x = lambda pi)
+ *   T_i   = sum_j pi_ij C_ij / (1 - rho_j)   (processor sharing: E[N_j] + 1 = 1/(1 - rho_j))
+ *   T     = (1/I) sum_i T_i                   (the mean over devices of Eq. (1)'s terms)
+ * An RRH with rho_j >= 1 that carries any of a device's traffic makes that device's time
+ * infinite (the queue is unstable), and T is +inf.  rho_out (J) is optional.
+ */
+int oracle_completion(const double* C, const double* x, const double* lam, int64_t I, int64_t J,
+                      double* T_out, double* rho_out) {
+    if (I <= 0 || J <= 0) return ORC_EINVAL;
+    double* rho = (double*)calloc((size_t)J, sizeof(double));
+    if (!rho) return ORC_ENOMEM;
+    for (int64_t i = 0; i < I; ++i)
+        for (int64_t j = 0; j < J; ++j) rho[j] += C[i * J + j] * x[i * J + j];
+    double T = 0.0;
+    for (int64_t i = 0; i < I; ++i) {
+        if (!(lam[i] > 0.0)) {
+            free(rho);
+            return ORC_EINVAL;
+        }
+        double Ti = 0.0;
+        for (int64_t j = 0; j < J; ++j) {
+            const double pij = x[i * J + j] / lam[i];
+            if (pij == 0.0) continue;
+            if (rho[j] >= 1.0) {
+                Ti = INFINITY;
+                break;
+            }
+            Ti += pij * C[i * J + j] / (1.0 - rho[j]);
+        }
+        T += Ti;
+    }
+    *T_out = T / (double)I;
+    if (rho_out) memcpy(rho_out, rho, (size_t)J * sizeof(double));
+    free(rho);
+    return ORC_OK;
+}
+
+/*
+ * Euclidean cost, Sec. IV choice (i): C_ij = || x_i - x_j || between device i at
+ * dev_xy[2i], dev_xy[2i+1] and RRH j at rrh_xy[2j], rrh_xy[2j+1] (metres).
+ */
+int oracle_euclid_cost(const double* dev_xy, const double* rrh_xy, int64_t I, int64_t J, double* C_out) {
+    if (I <= 0 || J <= 0) return ORC_EINVAL;
+    for (int64_t i = 0; i < I; ++i)
+        for (int64_t j = 0; j < J; ++j) {
+            const double dx = dev_xy[2 * i] - rrh_xy[2 * j];
+            const double dy = dev_xy[2 * i + 1] - rrh_xy[2 * j + 1];
+            C_out[i * J + j] = sqrt(dx * dx + dy * dy);
+        }
+    return ORC_OK;
 }

@@ -458,3 +458,104 @@ def test_adaptive_moves_delta_off_the_most_loaded_rrh():
     want = np.full(3, 1 / 3 + delta / 2)
     want[js] = 1 / 3 - delta
     np.testing.assert_allclose(q, want, rtol=1e-13)
+
+
+def test_adaptive_trace_matches_its_own_steps():
+    # the trace's j* is the argmax (lowest index on ties) of the same step's loads, its max
+    # load is that entry, and replaying the q updates from the trace reproduces the final q
+    rng = _rng(19)
+    C = rng.uniform(0, 1, (40, 5))
+    C[:, 1] *= 0.3
+    lam = rng.uniform(0.5, 1.5, 40)
+    delta = 0.01 * lam.sum()
+    f, g, q, ml, js, rho = oracle.adaptive_trace(C, lam, 0.05, 1e-12, 100000, 6, delta)
+    for s in range(6):
+        assert js[s] == int(np.argmax(rho[s]))
+        assert ml[s] == rho[s, js[s]]
+    qq = np.full(5, lam.sum() / 5)
+    for s in range(5):
+        d = delta if delta < qq[js[s]] else 0.5 * qq[js[s]]
+        qq = qq + d / 4
+        qq[js[s]] -= d + d / 4
+    np.testing.assert_allclose(q, qq, rtol=1e-13)
+    # the final plan is the last solve's, with the q it used
+    f2, g2, _, _ = oracle.sinkhorn(C, lam, q, 0.05, 1e-12, 100000, g0=None)
+    _, rho2, _, _ = oracle.finalize(C, f2, g2, lam, q, 0.05)
+    np.testing.assert_allclose(rho2, rho[-1], rtol=1e-9)
+
+
+def test_adaptive_half_move_when_delta_exceeds_the_target():
+    # delta larger than every target: each step halves the chosen RRH's target (mass kept)
+    rng = _rng(20)
+    C = rng.uniform(0, 1, (25, 3))
+    lam = np.full(25, 0.04)
+    _, _, q, _, js, _ = oracle.adaptive_trace(C, lam, 0.1, 1e-12, 100000, 2, 5.0)
+    want = np.full(3, 1 / 3)
+    want += (1 / 6) / 2
+    want[js[0]] = 1 / 3 - 1 / 6
+    np.testing.assert_allclose(q, want, rtol=1e-14)
+    assert q.sum() == pytest.approx(1.0, rel=1e-15)
+
+
+# ------------------------------------------------------------------ completion time (Sec. II-B)
+def test_completion_time_hand_worked_assignment():
+    # device 0 -> RRH 0, device 1 -> RRH 1 (hard association)
+    C = np.array([[0.5, 2.0], [3.0, 0.25]])
+    lam = np.array([0.4, 2.0])
+    x = np.array([[0.4, 0.0], [0.0, 2.0]])
+    T, rho = oracle.completion_time(C, x, lam)
+    # rho_0 = 0.4 * 0.5 = 0.2, rho_1 = 2 * 0.25 = 0.5
+    np.testing.assert_allclose(rho, [0.2, 0.5], rtol=1e-15)
+    # T_0 = 0.5 / 0.8, T_1 = 0.25 / 0.5
+    assert T == pytest.approx(0.5 * (0.625 + 0.5), rel=1e-15)
+
+
+def test_completion_time_split_plan_and_overload():
+    C = np.array([[1.0, 2.0], [0.5, 0.5]])
+    lam = np.array([0.2, 0.4])
+    x = np.array([[0.1, 0.1], [0.0, 0.4]])  # device 0 splits its time equally
+    T, rho = oracle.completion_time(C, x, lam)
+    np.testing.assert_allclose(rho, [0.1, 0.4], rtol=1e-15)  # 0.1 * 1; 0.1 * 2 + 0.4 * 0.5
+    T0 = 0.5 * 1.0 / 0.9 + 0.5 * 2.0 / 0.6
+    T1 = 1.0 * 0.5 / 0.6
+    assert T == pytest.approx(0.5 * (T0 + T1), rel=1e-14)
+    # RRH 1 overloaded: every device that uses it waits forever
+    T, rho = oracle.completion_time(C * 4, x, lam)
+    assert rho[1] >= 1.0 and math.isinf(T)
+    # an overloaded RRH that nobody uses changes nothing for the others
+    x2 = np.array([[0.2, 0.0], [0.4, 0.0]])
+    C2 = np.array([[1.0, 50.0], [0.5, 50.0]])
+    T, rho = oracle.completion_time(C2, x2, lam)
+    assert rho[1] == 0.0 and T == pytest.approx(0.5 * (1.0 / 0.6 + 0.5 / 0.6), rel=1e-14)
+
+
+def test_completion_time_of_maxsinr_against_brute_force():
+    # the maxSINR association as a 0/1 plan, summed device by device in Python
+    inst = ins.config1()
+    I = 200
+    R = oracle.rates(inst.G[:I], inst.P, inst.N0, inst.W_hz)
+    C = oracle.cost(R, inst.mu)
+    lam = inst.lam[:I] * 20.0  # enough traffic for visible queueing
+    assoc, Lam, tot = oracle.maxsinr(R, C, lam)
+    x = np.zeros_like(C)
+    x[np.arange(I), assoc] = lam
+    T, rho = oracle.completion_time(C, x, lam)
+    rho_bf = np.zeros(C.shape[1])
+    for i in range(I):
+        rho_bf[assoc[i]] += lam[i] * C[i, assoc[i]]
+    assert rho_bf.max() < 1.0
+    np.testing.assert_allclose(rho, rho_bf, rtol=1e-13)
+    T_bf = sum(C[i, assoc[i]] / (1.0 - rho_bf[assoc[i]]) for i in range(I)) / I
+    assert T == pytest.approx(T_bf, rel=1e-13)
+    assert rho.sum() == pytest.approx(tot, rel=1e-13)  # Lemma 1: total load of maxSINR
+
+
+# ------------------------------------------------------------------- Euclidean cost (Sec. IV)
+def test_euclid_cost_triangles():
+    dev = np.array([[0.0, 0.0], [3.0, 4.0], [-6.0, 8.0]])
+    rrh = np.array([[0.0, 0.0], [3.0, 0.0]])
+    C = oracle.euclid_cost(dev, rrh)
+    want = np.array([[0.0, 3.0], [5.0, 4.0], [10.0, math.hypot(9.0, 8.0)]])
+    np.testing.assert_allclose(C, want, rtol=1e-15)
+    # swapping the roles transposes the matrix
+    np.testing.assert_allclose(oracle.euclid_cost(rrh, dev), C.T, rtol=0, atol=0)
