@@ -643,6 +643,91 @@ def run_c5(args):
     return 0
 
 
+def run_alg2(args):
+    """Algorithm 2 (adaptive Sinkhorn association) on the 50,000 x 800 hot-spot instance:
+    `--alg2-outer` outer steps at eps = 0.1 median(C), delta = 5% of one RRH's equal share,
+    in one persistent launch; against the same steps driven from the host (one solve per
+    step, argmax and the q update on the host)."""
+    import torch
+
+    from paper_1805_01559_gb300 import binding
+    inst = make_inputs()
+    I, J = inst.I, inst.J
+    dev = torch.device("cuda", 0)
+    ctx = binding.Context(0)
+    G = torch.from_numpy(np.ascontiguousarray(inst.G, dtype=np.float32)).to(dev)
+    R = ctx.build_rates(G, torch.from_numpy(inst.P.astype(np.float32)).to(dev), inst.N0, inst.W_hz)
+    C, med = ctx.build_cost(R, inst.mu, eps_rel=1.0)
+    del G, R
+    lam = torch.from_numpy(inst.lam.astype(np.float32)).to(dev)
+    eps = 0.1 * med
+    outer = args.alg2_outer
+    delta = 0.05 * float(inst.lam.sum()) / J
+    s = torch.cuda.current_stream()
+
+    def fused():
+        return ctx.adaptive(C, lam, eps, delta, outer, tol=TOL, max_iter=MAX_ITER)
+
+    def host_loop():
+        q = np.full(J, float(inst.lam.astype(np.float32).astype(np.float64).sum()) / J)
+        g = None
+        its, ml = [], []
+        for k in range(outer):
+            r = ctx.solve_cost(C, lam, torch.from_numpy(q.astype(np.float32)).to(dev), eps, tol=TOL,
+                               max_iter=MAX_ITER, warm_g=g)
+            g = r.g
+            rho = r.rrh_load.cpu().numpy()
+            js = int(np.argmax(rho))
+            its.append(r.iters)
+            ml.append(float(rho[js]))
+            if k + 1 < outer:
+                d = delta if delta < q[js] else 0.5 * q[js]
+                q = np.where(np.arange(J) == js, q - d, q + d / (J - 1))
+        return its, ml
+
+    for _ in range(args.warmup):
+        fused()
+        host_loop()
+    ms_f, ms_h, iters = [], [], None
+    ctx.enable_timing(False)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = ctx.launch_count()
+    for _ in range(args.steps):
+        res, ms, _ = _timed(fused, s)
+        ms_f.append(ms)
+    launches = (ctx.launch_count() - l0) / args.steps
+    clk = clocks.stop()
+    for _ in range(max(1, args.steps // 2)):
+        (its_h, ml_h), ms, _ = _timed(host_loop, s)
+        ms_h.append(ms)
+    iters = [st["iters"] for st in res.steps]
+    ml = [st["max_load"] for st in res.steps]
+    ms = statistics.median(ms_f)
+    cells_iters = float(I) * J * sum(iters)
+    alg_bytes = 4.0 * I * J * sum(it + 2 for it in iters)
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": cells_iters / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"alg2_adaptive_50000x800: {outer} outer steps, eps = 0.1 median(C), "
+                                   f"delta = 5% of an equal share", "I": I, "J": J, "outer": outer, "tol": TOL,
+                       "l2": "C (160 MB) larger than L2"},
+            "outer_steps_per_s": outer / (ms / 1e3),
+            "host_loop": {"ms": statistics.median(ms_h), "iters": its_h,
+                          "fused_speedup": statistics.median(ms_h) / ms},
+            "iters": iters, "max_load": {"first": ml[0], "last": ml[-1], "min": min(ml)},
+            "jstar": [st["jstar"] for st in res.steps],
+            "roofline": {"bound": "hbm", "kernel": "sk_adaptive (whole launch)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "alg_bytes_per_launch": alg_bytes},
+            "gpu_launches": launches, "clocks": clk}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -653,8 +738,10 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=12_500)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="only run this many rounds of the three solves of one step (for profiler captures)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
-                    help="c2: the headline line; c3 batched ragged; c4 stored-kernel precision; c5 serving")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2"],
+                    help="c2: the headline line; c3 batched ragged; c4 stored-kernel precision; c5 serving; "
+                         "alg2 adaptive association (Algorithm 2)")
+    ap.add_argument("--alg2-outer", type=int, default=20)
     ap.add_argument("--c3-instances", type=int, default=256)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--c4-rows", type=int, default=400_000)
@@ -665,7 +752,7 @@ def main():
     if args.profile_solves > 0:
         return run_profile_solve(args)
     if args.workload != "c2" and args.impl != "reference":
-        return {"c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
+        return {"c3": run_c3, "c4": run_c4, "c5": run_c5, "alg2": run_alg2}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -349,6 +349,95 @@ ot_status ot_assoc_tuning_set(ot_assoc_ctx* ctx, int32_t bucket, int32_t gsize, 
 /* Size bucket of an I x J instance. */
 int32_t ot_assoc_bucket(int64_t I, int32_t J);
 
+/* ---------------------------------------------------------------------------------------
+ * Policy evaluation (Sec. II-B, Sec. IV).
+ * ------------------------------------------------------------------------------------- */
+/* Euclidean cost, Sec. IV cost choice (i): C_ij = ||x_i - x_j|| in the coordinates' unit.
+ * dev_xy [device] float I x 2 (x, y per device), rrh_xy [device] float J x 2, both 8-byte
+ * aligned; C_out [device] float I x J, ld_c (0 = J).  Formed in FP64, rounded once to FP32.
+ * Only enqueues. */
+ot_status ot_assoc_euclid_cost(ot_assoc_ctx* ctx, const float* dev_xy, const float* rrh_xy, int64_t I,
+                               int64_t J, float* C_out, int64_t ld_c, void* stream);
+
+/* Average job completion time of an association, Sec. II-B (processor sharing at each RRH):
+ *   rho_j = sum_i C_ij x_ij,  T = (1/I) sum_i sum_j pi_ij C_ij / (1 - rho_j),
+ * with C [device] float I x J (ld_c, 0 = J) the LOAD cost 1/(mu R_ij), x the plan in mass
+ * units and pi_ij = x_ij / lambda_i the association fractions.  The plan is either
+ *   assoc   [device] int32 I: hard association (x_ij = lambda_i when j = assoc_i), or, when
+ *           assoc is NULL, the entropic plan x_ij = exp((f_i + g_j - Cp_ij) / eps) of
+ *           potentials f [device] double I, g [device] double J on the plan cost Cp =
+ *           C_plan [device] float I x J (ld_plan, 0 = J), or on C itself when C_plan is NULL.
+ * traffic [device] float I, lambda_i > 0 (OT_EINVAL otherwise).  rho_out [device] double J
+ * or NULL.  T_out [host]: +inf when an RRH that carries traffic has rho_j >= 1.  Column sums
+ * are FP64 in a fixed order (deterministic).  Synchronises `stream`. */
+ot_status ot_assoc_completion_time(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* traffic,
+                                   int64_t I, int64_t J, const int32_t* assoc, const float* C_plan,
+                                   int64_t ld_plan, const double* f, const double* g, double eps,
+                                   double* rho_out, double* T_out, void* stream);
+
+/* Mean over the I rows of min_j C_ij (each device's cheapest link), FP64 sums in a fixed
+ * order.  C [device] float I x J (ld_c, 0 = J); *out [host].  Synchronises `stream`.  Used as
+ * the scale of eps in the policy comparison (a regularisation relative to the cost of the
+ * links a plan actually uses). */
+ot_status ot_assoc_mean_row_min(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, int64_t I, int64_t J,
+                                double* out, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Adaptive Sinkhorn association (Algorithm 2, Sec. V) in ONE persistent launch.
+ * The RRH targets start from the equal split q_j = sum_i lambda_i / J (Algorithm 2,
+ * initialisation).  Each outer step s:
+ *   1. solves Algorithm 1 with (C, p = lambda, q^(s), eps), exactly as
+ *      ot_assoc_solve_cost does (same arithmetic and stopping rule); steps after the first
+ *      start from the previous step's g unless cold_start is set;
+ *   2. finalizes the plan in FP64 and forms the RRH loads rho_j = sum_i C_ij pi_ij
+ *      (Sec. II-B with x = pi the mass plan);
+ *   3. picks j* = argmax_j rho_j (lowest index on ties), "step 5" of Algorithm 2;
+ *   4. unless it is the last step, sets q_j* -= d and q_j += d / (J - 1) for j != j*, with
+ *      d = delta, or d = q_j* / 2 when delta >= q_j* (a target never reaches zero).
+ * The paper gives no stopping rule for the outer loop, so exactly `outer` steps run; the
+ * outputs are the last step's plan and the q it used.  The targets are updated in FP64.
+ * Arguments:
+ *   C        [device] float I x J cost, ld_c (0 = J), 16-byte aligned rows, ld_c % 4 == 0
+ *   traffic  [device] float I, lambda_i > 0
+ *   prm      [host]   parameters below
+ *   f, g     [device] double I and J: potentials of the last step's plan (required; g is
+ *            also the warm-start buffer between steps, so its input value is ignored)
+ *   q_out    [device] double J: targets used by the last solve (required; the FP64 state)
+ *   rrh_load [device] double J: rho_j of the last plan, or NULL
+ *   pi, pi_ld [device] float I x J plan of the last step (mass units), or NULL
+ *   steps    [host]   outer entries, filled per step (below)
+ * Limits: 2 <= J <= 1024 (OT_EUNSUPPORTED above), I >= 1.  Synchronises `stream`.
+ * Returns OT_OK when every step converged, OT_NOT_CONVERGED when some step stopped at
+ * max_iter (results valid), or the first failing step's error (later steps then carry
+ * that status and did not run).
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    double eps;         /* > 0, absolute (every step) */
+    double tol;         /* >= 0, row residual of the unit-mass plan */
+    double delta;       /* >= 0, traffic moved off the most loaded RRH per step (units of lambda) */
+    int32_t max_iter;   /* >= 1, Sinkhorn iterations per step */
+    int32_t outer;      /* >= 1, outer steps */
+    int32_t cold_start; /* != 0: every step starts from g = 0 */
+    int32_t reserved;
+} ot_assoc_adaptive_params;
+
+typedef struct {
+    double max_load;       /* rho_j* of this step's plan */
+    double transport_cost; /* sum_ij C_ij pi_ij of this step's plan */
+    double marg_err_row;   /* FP64 residuals of this step's plan (unit mass) */
+    double marg_err_col;
+    double err_loop;       /* residual estimate that stopped the step's loop */
+    int32_t jstar;         /* most loaded RRH (-1 when the step did not complete) */
+    int32_t iters;         /* Sinkhorn iterations of this step */
+    int32_t converged;
+    int32_t status;        /* OT_OK, OT_NOT_CONVERGED, or an error */
+} ot_assoc_adaptive_step;
+
+ot_status ot_assoc_adaptive(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* traffic,
+                            int64_t I, int64_t J, const ot_assoc_adaptive_params* prm, double* f,
+                            double* g, double* q_out, double* rrh_load, float* pi, int64_t pi_ld,
+                            ot_assoc_adaptive_step* steps, void* stream);
+
 
 /* ---------------------------------------------------------------------------------------
  * Serving (the paper has no counterpart: a service of the library around Algorithm 1).

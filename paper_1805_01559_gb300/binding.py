@@ -734,3 +734,111 @@ def _device_view(ptr: int, shape, typestr: str) -> torch.Tensor:
 
 
 Context.server = lambda self, **kw: Server(self, **kw)
+
+
+# ---- adaptive Sinkhorn association (Algorithm 2) ----------------------------------------------
+class ot_assoc_adaptive_params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("tol", ctypes.c_double), ("delta", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("outer", ctypes.c_int32), ("cold_start", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ot_assoc_adaptive_step(ctypes.Structure):
+    _fields_ = [("max_load", ctypes.c_double), ("transport_cost", ctypes.c_double),
+                ("marg_err_row", ctypes.c_double), ("marg_err_col", ctypes.c_double), ("err_loop", ctypes.c_double),
+                ("jstar", ctypes.c_int32), ("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
+SIGNATURES["ot_assoc_adaptive"] = (ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _I64,
+                                                  ctypes.POINTER(ot_assoc_adaptive_params), _VP, _VP, _VP, _VP,
+                                                  _VP, _I64, ctypes.POINTER(ot_assoc_adaptive_step), _VP])
+if _lib is not None:
+    _lib.ot_assoc_adaptive.restype, _lib.ot_assoc_adaptive.argtypes = SIGNATURES["ot_assoc_adaptive"]
+
+
+@dataclasses.dataclass
+class AdaptiveResult:
+    f: torch.Tensor
+    g: torch.Tensor
+    q: torch.Tensor                    # FP64 targets the last solve used
+    rrh_load: torch.Tensor             # rho_j of the last plan
+    pi: Optional[torch.Tensor]
+    steps: list                        # per outer step: dict(jstar, max_load, iters, ...)
+    status: int
+
+
+def _ctx_adaptive(self, C, traffic, eps, delta, outer, tol=1e-6, max_iter=2000, cold_start=False,
+                  want_pi=False, stream=None) -> AdaptiveResult:
+    """Algorithm 2: `outer` steps of (solve with q, most loaded RRH j*, move delta off j*)."""
+    _need(C, torch.float32, "C", 2)
+    _need(traffic, torch.float32, "traffic", 1)
+    I, J = C.shape
+    dev = C.device
+    f = torch.empty(I, dtype=torch.float64, device=dev)
+    g = torch.empty(J, dtype=torch.float64, device=dev)
+    q = torch.empty(J, dtype=torch.float64, device=dev)
+    load = torch.empty(J, dtype=torch.float64, device=dev)
+    pi = torch.empty((I, J), dtype=torch.float32, device=dev) if want_pi else None
+    prm = ot_assoc_adaptive_params(eps=float(eps), tol=float(tol), delta=float(delta), max_iter=int(max_iter),
+                                   outer=int(outer), cold_start=int(bool(cold_start)), reserved=0)
+    steps = (ot_assoc_adaptive_step * max(1, int(outer)))()
+    st = self._L.ot_assoc_adaptive(self._h, _ptr(C), C.stride(0), _ptr(traffic), I, J, ctypes.byref(prm),
+                                   _ptr(f), _ptr(g), _ptr(q), _ptr(load), _ptr(pi), J if want_pi else 0, steps,
+                                   _stream(stream))
+    self._check(st, allow_nc=True)
+    out = [{k: getattr(s, k) for k, _ in ot_assoc_adaptive_step._fields_} for s in steps[:int(outer)]]
+    return AdaptiveResult(f=f, g=g, q=q, rrh_load=load, pi=pi, steps=out, status=st)
+
+
+Context.adaptive = _ctx_adaptive
+
+
+# ---- policy evaluation: Euclidean cost, completion time (Sec. II-B, Sec. IV) -------------------
+SIGNATURES["ot_assoc_euclid_cost"] = (ctypes.c_int, [_VP, _VP, _VP, _I64, _I64, _VP, _I64, _VP])
+SIGNATURES["ot_assoc_completion_time"] = (ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _I64, _VP, _VP, _I64, _VP,
+                                                         _VP, _D, _VP, _PD, _VP])
+if _lib is not None:
+    for _name in ("ot_assoc_euclid_cost", "ot_assoc_completion_time"):
+        _fn = getattr(_lib, _name)
+        _fn.restype, _fn.argtypes = SIGNATURES[_name]
+
+
+def _ctx_euclid_cost(self, dev_xy, rrh_xy, C_out=None, stream=None) -> torch.Tensor:
+    """C_ij = ||x_i - x_j|| (Sec. IV cost choice (i)); dev_xy I x 2, rrh_xy J x 2 float32."""
+    _need(dev_xy, torch.float32, "dev_xy", 2)
+    _need(rrh_xy, torch.float32, "rrh_xy", 2)
+    if not dev_xy.is_contiguous() or not rrh_xy.is_contiguous() or dev_xy.shape[1] != 2 or rrh_xy.shape[1] != 2:
+        raise ValueError("coordinates must be contiguous (n, 2) tensors")
+    I, J = dev_xy.shape[0], rrh_xy.shape[0]
+    if C_out is None:
+        ld = (J + 3) // 4 * 4
+        C_out = torch.empty((I, ld), dtype=torch.float32, device=dev_xy.device)[:, :J]
+    _need(C_out, torch.float32, "C_out", 2)
+    self._check(self._L.ot_assoc_euclid_cost(self._h, _ptr(dev_xy), _ptr(rrh_xy), I, J, _ptr(C_out),
+                                             C_out.stride(0), _stream(stream)))
+    return C_out
+
+
+def _ctx_completion_time(self, C, traffic, assoc=None, f=None, g=None, eps=0.0, C_plan=None, want_rho=True,
+                         stream=None):
+    """Average job completion time (Sec. II-B) of a hard association or of the entropic plan of
+    potentials (f, g) on C_plan (default C); C is the load cost.  Returns (T, rho)."""
+    _need(C, torch.float32, "C", 2)
+    _need(traffic, torch.float32, "traffic", 1)
+    I, J = C.shape
+    if assoc is not None:
+        _need(assoc, torch.int32, "assoc", 1)
+    if C_plan is not None:
+        _need(C_plan, torch.float32, "C_plan", 2)
+    rho = torch.empty(J, dtype=torch.float64, device=C.device) if want_rho else None
+    T = ctypes.c_double(0.0)
+    self._check(self._L.ot_assoc_completion_time(
+        self._h, _ptr(C), C.stride(0), _ptr(traffic), I, J, _ptr(assoc), _ptr(C_plan),
+        C_plan.stride(0) if C_plan is not None else 0, _ptr(f), _ptr(g), float(eps), _ptr(rho), ctypes.byref(T),
+        _stream(stream)))
+    return T.value, rho
+
+
+Context.euclid_cost = _ctx_euclid_cost
+Context.completion_time = _ctx_completion_time

@@ -85,7 +85,7 @@ __device__ __forceinline__ bool bt_finalize(const BInst& D, const SolveParams& P
             s = warp_sum(s);
             r = warp_sum(r);
             if (lane == 0) {
-                ec += fabs(s - (double)__ldg(P.q + j) * inv_sq);
+                ec += fabs(s - (double)__ldcg(P.q + j) * inv_sq);
                 co += r;
                 if (D.rrh_load) D.rrh_load[j] = r * sp;
                 D.g_out[j] = D.eps_ln2 * Gk[j];

@@ -613,7 +613,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
         int badq = 0;
         for (int bb = tid; bb < V; bb += NC) a += P.errpart[bb];
         for (int j = tid; j < J; j += NC) {
-            const float x = __ldg(P.q + j);
+            const float x = __ldcg(P.q + j);
             badq |= !(x > 0.0f) || !isfinite(x);
             c += (double)x;
         }
@@ -649,7 +649,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
     double* LQ = P.G + 2 * Jp;  // log2 q^_j, formed once here (read after the next grid barrier)
     {
         const int gw = b * NCW + warp, nw = nb * NCW;
-        for (int j = gw * 32 + lane; j < J; j += nw * 32) LQ[j] = log2((double)__ldg(P.q + j) * inv_sq);
+        for (int j = gw * 32 + lane; j < J; j += nw * 32) LQ[j] = log2((double)__ldcg(P.q + j) * inv_sq);
         const float inv_sp_f = (float)(1.0 / sp);
         for (int r = tid; r < nrow; r += NC) Ps[r] *= inv_sp_f;  // p^_i
         bar_named(CONS_BAR, NC);
