@@ -728,6 +728,62 @@ def run_alg2(args):
     return 0
 
 
+def run_policies(args):
+    """Sec. IV's uniform-traffic comparison: 25 RRHs in 1 km^2, N devices, policies (a)
+    maxSINR, (b) OT Euclidean cost + equal RRH traffic, (c) OT load cost + equal traffic,
+    (d) OT load cost + q = Lambda (Lemma 1); completion-time ratios to (a).  All cells' OT
+    solves run as one batched launch."""
+    import torch
+
+    from paper_1805_01559_gb300 import binding, instances as ins, policies
+    ctx = binding.Context(0)
+    sizes = (100, 200, 500, 1000, 2000, 5000)
+    seeds = range(args.policy_seeds)
+    cells = [(N, sd, ins.policy_cell(N, sd)) for N in sizes for sd in seeds]
+    s = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    preps = [policies.prepare(ctx, c, load_target=0.3, eps_best=0.01, tol=TOL, max_iter=MAX_ITER)
+             for _, _, c in cells]
+    prep_s = time.perf_counter() - t0
+    insts = [x for p in preps for x in p.instances]
+    for _ in range(args.warmup):
+        ctx.solve_batched(insts)
+    ms_all = []
+    for _ in range(args.steps):
+        res, ms, _ = _timed(lambda: ctx.solve_batched(insts), s)
+        ms_all.append(ms)
+    ms = statistics.median(ms_all)
+    t1 = time.perf_counter()
+    out = [policies.finish(ctx, p, res[3 * k: 3 * k + 3]) for k, p in enumerate(preps)]
+    fin_s = time.perf_counter() - t1
+    table = {}
+    for N in sizes:
+        rs = [o for (n, _, _), o in zip(cells, out) if n == N]
+        row = {}
+        for k in "bcd":
+            v = np.array([o.ratio[k] for o in rs])
+            fin = v[np.isfinite(v)]
+            row[k] = {"median": float(np.median(v)) if len(v) else None,
+                      "median_finite": float(np.median(fin)) if len(fin) else None,
+                      "unstable": int((~np.isfinite(v)).sum())}
+        table[str(N)] = row
+    cells_iters = sum(x.C.shape[0] * x.C.shape[1] * r.iters for x, r in zip(insts, res))
+    line = {"metric": "policy OT solves/s", "value": len(insts) / (ms / 1e3), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"policies_25rrh: N in {list(sizes)}, {len(seeds)} drops each, "
+                                   f"{len(insts)} OT solves in one batched launch",
+                       "load_target": 0.3, "eps": "0.01 x mean cheapest-link cost", "tol": TOL,
+                       "max_iter": MAX_ITER},
+            "cells_iters_per_s": cells_iters / (ms / 1e3),
+            "completion_time_ratio_to_maxsinr": table,
+            "prepare_s": prep_s, "finish_s": fin_s,
+            "not_converged": int(sum(1 for r in res if not r.converged))}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -738,10 +794,11 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=12_500)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="only run this many rounds of the three solves of one step (for profiler captures)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2", "policies"],
                     help="c2: the headline line; c3 batched ragged; c4 stored-kernel precision; c5 serving; "
                          "alg2 adaptive association (Algorithm 2)")
     ap.add_argument("--alg2-outer", type=int, default=20)
+    ap.add_argument("--policy-seeds", type=int, default=8)
     ap.add_argument("--c3-instances", type=int, default=256)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--c4-rows", type=int, default=400_000)
@@ -752,7 +809,8 @@ def main():
     if args.profile_solves > 0:
         return run_profile_solve(args)
     if args.workload != "c2" and args.impl != "reference":
-        return {"c3": run_c3, "c4": run_c4, "c5": run_c5, "alg2": run_alg2}[args.workload](args)
+        return {"c3": run_c3, "c4": run_c4, "c5": run_c5, "alg2": run_alg2,
+                "policies": run_policies}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -383,6 +383,25 @@ ot_status ot_assoc_mean_row_min(ot_assoc_ctx* ctx, const float* C, int64_t ld_c,
                                 double* out, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * eps-scaling (annealing) for Algorithm 1, in ONE persistent launch.  Stages solve Eq. (5)
+ * at eps_s = eps0 * factor^s while that is above eps, then at eps itself; each stage starts
+ * from the previous stage's g (the first from b = 1, or from the caller's g when warm_start).
+ * Intermediate stages stop at residual <= tol_stage, the last at tol; every stage is capped
+ * at max_iter iterations.  The result is the solution at `eps` exactly as ot_assoc_solve_cost
+ * defines it (same arithmetic and stopping rule); the stages only choose where its iteration
+ * starts.  Arguments as ot_assoc_solve_cost, plus:
+ *   eps0 >= eps, 0 < factor < 1 (at most 64 stages);
+ *   stage_iters [host] int32 per stage (<= 64 entries) or NULL; *nstages_out [host] or NULL.
+ * out->iters is the total over the stages; the summary is the last stage's.  Limits: J <= 1024,
+ * C 16-byte aligned with ld_c % 4 == 0.  Synchronises `stream`.
+ * ------------------------------------------------------------------------------------- */
+ot_status ot_assoc_solve_eps_scaling(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* p,
+                                     const float* q, int64_t I, int64_t J, double eps, double eps0,
+                                     double factor, double tol_stage, double tol, int32_t max_iter,
+                                     int32_t warm_start, ot_assoc_result* out, int32_t* stage_iters,
+                                     int32_t* nstages_out, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Adaptive Sinkhorn association (Algorithm 2, Sec. V) in ONE persistent launch.
  * The RRH targets start from the equal split q_j = sum_i lambda_i / J (Algorithm 2,
  * initialisation).  Each outer step s:

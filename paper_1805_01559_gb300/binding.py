@@ -842,3 +842,53 @@ def _ctx_completion_time(self, C, traffic, assoc=None, f=None, g=None, eps=0.0, 
 
 Context.euclid_cost = _ctx_euclid_cost
 Context.completion_time = _ctx_completion_time
+
+
+SIGNATURES["ot_assoc_mean_row_min"] = (ctypes.c_int, [_VP, _VP, _I64, _I64, _I64, _PD, _VP])
+if _lib is not None:
+    _lib.ot_assoc_mean_row_min.restype, _lib.ot_assoc_mean_row_min.argtypes = SIGNATURES["ot_assoc_mean_row_min"]
+
+
+def _ctx_mean_row_min(self, C, stream=None) -> float:
+    """Mean over rows of min_j C_ij (the cost of each device's cheapest link)."""
+    _need(C, torch.float32, "C", 2)
+    out = ctypes.c_double(0.0)
+    self._check(self._L.ot_assoc_mean_row_min(self._h, _ptr(C), C.stride(0), C.shape[0], C.shape[1],
+                                              ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+Context.mean_row_min = _ctx_mean_row_min
+
+
+# ---- eps-scaling ----------------------------------------------------------------------------------
+SIGNATURES["ot_assoc_solve_eps_scaling"] = (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _D, _D,
+                                                           _D, _I32, _I32, ctypes.POINTER(ot_assoc_result),
+                                                           ctypes.POINTER(ctypes.c_int32),
+                                                           ctypes.POINTER(ctypes.c_int32), _VP])
+if _lib is not None:
+    _lib.ot_assoc_solve_eps_scaling.restype, _lib.ot_assoc_solve_eps_scaling.argtypes = \
+        SIGNATURES["ot_assoc_solve_eps_scaling"]
+
+
+def _ctx_solve_eps_scaling(self, C, p, q, eps, eps0, factor=0.3, tol_stage=1e-3, tol=1e-6, max_iter=2000,
+                           warm_g=None, want_pi=False, want_load=True, stream=None):
+    """Algorithm 1 at eps, started through the stages eps0 * factor^s (eps-scaling).
+    Returns (Result, per-stage iteration counts)."""
+    _need(C, torch.float32, "C", 2)
+    _need(p, torch.float32, "p", 1)
+    _need(q, torch.float32, "q", 1)
+    I, J = C.shape
+    g = warm_g.clone() if warm_g is not None else None
+    r, f, g, pi, load = self._result(I, J, C.device, want_pi, want_load, None, g)
+    its = (ctypes.c_int32 * 64)()
+    ns = ctypes.c_int32(0)
+    st = self._L.ot_assoc_solve_eps_scaling(self._h, _ptr(C), C.stride(0), _ptr(p), _ptr(q), I, J, float(eps),
+                                            float(eps0), float(factor), float(tol_stage), float(tol),
+                                            int(max_iter), int(warm_g is not None), ctypes.byref(r), its,
+                                            ctypes.byref(ns), _stream(stream))
+    self._check(st, allow_nc=True)
+    return self._pack(r, f, g, pi, load), list(its[:ns.value])
+
+
+Context.solve_eps_scaling = _ctx_solve_eps_scaling

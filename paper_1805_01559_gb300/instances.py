@@ -344,3 +344,28 @@ def config4_blocked(seed: int = 0, I: int = 400_000, J: int = 4096, block: int =
     return BlockedInstance(name=f"c4_{I}x{J}", I=I, J=J, side=side, seed=seed, block=block, rrh_xy=rrh,
                            dev_xy=dev, P=np.full(J, P_TX_W), N0=noise_power_w(), W_hz=W_HZ, mu=MU_PER_BIT,
                            lam=lam, q=q)
+
+
+@dataclasses.dataclass
+class PolicyCell:
+    """A cell of the uniform-traffic policy comparison (Sec. IV): J RRHs on a jittered grid,
+    N devices uniform in the square, distance-only path loss (no shadowing), equal traffic
+    per device (unit total; the comparison scales it)."""
+    G: np.ndarray        # N x J gains (float32)
+    P: np.ndarray        # J powers
+    N0: float
+    W_hz: float
+    mu: float
+    dev_xy: np.ndarray   # N x 2 (float32)
+    rrh_xy: np.ndarray   # J x 2 (float32)
+    lam: np.ndarray      # N, equal, sum 1
+    side: float
+
+
+def policy_cell(N: int, seed: int, J: int = 25, side: float = 1000.0) -> PolicyCell:
+    rng = _rng(np.random.SeedSequence([seed, 11, N]))
+    rrh = rrh_jittered_grid(J, side, rng).astype(np.float32)
+    dev = devices_uniform(N, side, rng).astype(np.float32)
+    G = path_gains(dev.astype(np.float64), rrh.astype(np.float64), np.zeros((N, J), np.float32), dtype=np.float32)
+    return PolicyCell(G=G, P=np.full(J, P_TX_W), N0=noise_power_w(), W_hz=W_HZ, mu=MU_PER_BIT, dev_xy=dev,
+                      rrh_xy=rrh, lam=np.full(N, 1.0 / N), side=side)
