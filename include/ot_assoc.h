@@ -180,6 +180,25 @@ ot_status ot_assoc_solve_cost(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, c
                               void* stream);
 
 /*
+ * ot_assoc_solve_cost without waiting: the solve is enqueued on `stream` and *ticket [host]
+ * identifies it.  `out` supplies the device pointers (f, g, pi, rrh_load), which must stay
+ * valid until the solve completes; ot_assoc_wait fills the host fields.  Up to 16 solves may
+ * be in flight per context (OT_EBUSY beyond); they share the context's scratch, so they must
+ * be enqueued on ONE stream (they then run one after another).  Argument errors are returned
+ * at once; device-side outcomes (invalid input, numerical breakdown, timeout, not converged)
+ * by ot_assoc_wait.
+ */
+ot_status ot_assoc_solve_cost_async(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* p,
+                                    const float* q, int64_t I, int64_t J, double eps, double tol,
+                                    int32_t max_iter, int32_t warm_start, const ot_assoc_result* out,
+                                    uint64_t* ticket, void* stream);
+
+/* Block until the asynchronous solve `ticket` has completed and fill out's host fields
+ * (transport_cost, residuals, iters, status) as ot_assoc_solve_cost would; returns its
+ * status.  Each ticket can be waited for once (OT_EINVAL for an unknown ticket). */
+ot_status ot_assoc_wait(ot_assoc_ctx* ctx, uint64_t ticket, ot_assoc_result* out);
+
+/*
  * ot_assoc_solve_cost without any memory allocation (the paper has no counterpart: this
  * is a service of the library, not a step of the method).
  *
@@ -222,10 +241,11 @@ ot_status ot_assoc_solve_f64(ot_assoc_ctx* ctx, const double* C, int64_t ld_c, c
  * solve's stream around each phase; only while timing is enabled).
  */
 typedef struct {
-    double init_ms;      /* marginal sums + iteration 1 (exact log-domain step) */
-    double loop_ms;      /* persistent kernel: iterations 2.. (one read of C per sweep) */
-    double finalize_ms;  /* plan, potentials, FP64 reductions */
-    int32_t sweeps;      /* full reads of the cost/kernel matrix made by the persistent kernel */
+    double init_ms;      /* state reset before the persistent kernel */
+    double loop_ms;      /* the persistent kernel: setup, iteration 1, every later iteration,
+                            the finalize sweep (it reads C iters + 2 times) */
+    double finalize_ms;  /* FP64 column totals and the summary */
+    int32_t sweeps;      /* completed iterations (the kernel reads C sweeps + 2 times) */
     int32_t valid;       /* 1 when the fields above belong to the last solve */
 } ot_assoc_timings;
 

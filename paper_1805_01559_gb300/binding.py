@@ -892,3 +892,47 @@ def _ctx_solve_eps_scaling(self, C, p, q, eps, eps0, factor=0.3, tol_stage=1e-3,
 
 
 Context.solve_eps_scaling = _ctx_solve_eps_scaling
+
+
+# ---- asynchronous solves -----------------------------------------------------------------------
+SIGNATURES["ot_assoc_solve_cost_async"] = (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,
+                                                          ctypes.POINTER(ot_assoc_result),
+                                                          ctypes.POINTER(ctypes.c_uint64), _VP])
+SIGNATURES["ot_assoc_wait"] = (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ot_assoc_result)])
+if _lib is not None:
+    for _name in ("ot_assoc_solve_cost_async", "ot_assoc_wait"):
+        _fn = getattr(_lib, _name)
+        _fn.restype, _fn.argtypes = SIGNATURES[_name]
+
+
+class Pending:
+    """An enqueued solve (ot_assoc_solve_cost_async); wait() returns its Result."""
+
+    def __init__(self, ctx, ticket, r, f, g, pi, load):
+        self._ctx, self.ticket, self._r = ctx, ticket, r
+        self._bufs = (f, g, pi, load)
+
+    def wait(self) -> Result:
+        st = self._ctx._L.ot_assoc_wait(self._ctx._h, self.ticket, ctypes.byref(self._r))
+        self._ctx._check(st, allow_nc=True)
+        return self._ctx._pack(self._r, *self._bufs)
+
+
+def _ctx_solve_cost_async(self, C, p, q, eps, tol=1e-6, max_iter=2000, warm_g=None, want_pi=False, want_load=True,
+                          f=None, g=None, stream=None) -> Pending:
+    _need(C, torch.float32, "C", 2)
+    _need(p, torch.float32, "p", 1)
+    _need(q, torch.float32, "q", 1)
+    I, J = C.shape
+    if warm_g is not None:
+        g = warm_g if g is None else g.copy_(warm_g)
+    r, f, g, pi, load = self._result(I, J, C.device, want_pi, want_load, f, g)
+    ticket = ctypes.c_uint64(0)
+    st = self._L.ot_assoc_solve_cost_async(self._h, _ptr(C), C.stride(0), _ptr(p), _ptr(q), I, J, float(eps),
+                                           float(tol), int(max_iter), int(warm_g is not None), ctypes.byref(r),
+                                           ctypes.byref(ticket), _stream(stream))
+    self._check(st)
+    return Pending(self, ticket.value, r, f, g, pi, load)
+
+
+Context.solve_cost_async = _ctx_solve_cost_async

@@ -75,6 +75,18 @@ void* host_staging(ot_assoc_ctx* ctx, size_t bytes, ot_status* st) {
     return ctx->host_pinned;
 }
 
+cudaError_t allow_max_dynamic_smem(const void* fn, size_t need) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    const size_t limit = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if (need > limit) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+}
+
 void timing_mark(ot_assoc_ctx* ctx, int k, cudaStream_t s) {
     if (!ctx->timing) return;
     if (!ctx->ev[k] && cudaEventCreate(&ctx->ev[k]) != cudaSuccess) {
@@ -219,8 +231,12 @@ void ot_assoc_destroy(ot_assoc_ctx* ctx) {
     for (auto& b : ctx->slots)
         if (b.ptr) cudaFree(b.ptr);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+    if (ctx->async_sum) cudaFreeHost(ctx->async_sum);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& row : ctx->async_ev)
+        for (auto& e : row)
+            if (e) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -375,6 +391,87 @@ ot_status ot_assoc_solve_cost(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, c
     SolveSummary sum;
     st = launch_solve_f32(ctx, a, &sum);
     if (st) return st;
+    return finish(ctx, sum, out);
+}
+
+ot_status ot_assoc_solve_cost_async(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* p,
+                                    const float* q, int64_t I, int64_t J, double eps, double tol, int32_t max_iter,
+                                    int32_t warm_start, const ot_assoc_result* out, uint64_t* ticket,
+                                    void* stream) {
+    ot_status st = check_solve_args(ctx, C, p, q, I, J, ld_c, eps, tol, max_iter, out);
+    if (st) return st;
+    if (!ticket) return set_error(ctx, OT_EINVAL, "null ticket pointer");
+    if (ld_c == 0) ld_c = J;
+    DeviceGuard g(ctx->device);
+    if (!ctx->async_sum) {
+        cudaError_t e = cudaMallocHost(&ctx->async_sum, sizeof(SolveSummary) * ot_assoc_ctx::kAsyncSlots);
+        if (e != cudaSuccess) {
+            ctx->async_sum = nullptr;
+            return cuda_error(ctx, e, "cudaMallocHost (async summaries)");
+        }
+    }
+    int k = -1;
+    for (int i = 0; i < ot_assoc_ctx::kAsyncSlots; ++i)
+        if (ctx->async_ticket[i] == 0) {
+            k = i;
+            break;
+        }
+    if (k < 0) return set_error(ctx, OT_EBUSY, "%d asynchronous solves in flight: wait for one first",
+                                ot_assoc_ctx::kAsyncSlots);
+    for (auto& e : ctx->async_ev[k])
+        if (!e && cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, OT_ECUDA, "cudaEventCreate");
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveArgs a;
+    st = aligned_view(ctx, C, ld_c, I, (int)J, s, &a.C, &a.ld);
+    if (st) return st;
+    a.p = p;
+    a.q = q;
+    a.I = I;
+    a.J = (int)J;
+    a.eps = eps;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.warm_start = warm_start;
+    a.out = const_cast<ot_assoc_result*>(out);
+    a.stream = s;
+    SolveSummary* dest = (SolveSummary*)ctx->async_sum + k;
+    st = enqueue_solve_f32(ctx, a, dest, ctx->timing ? ctx->async_ev[k][1] : nullptr,
+                           ctx->timing ? ctx->async_ev[k][2] : nullptr);
+    if (st) return st;
+    cudaError_t e = cudaEventRecord(ctx->async_ev[k][0], s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "event record");
+    ctx->async_ticket[k] = ctx->next_ticket++;
+    *ticket = ctx->async_ticket[k];
+    return OT_OK;
+}
+
+ot_status ot_assoc_wait(ot_assoc_ctx* ctx, uint64_t ticket, ot_assoc_result* out) {
+    if (!ctx) return OT_EINVAL;
+    if (!out) return set_error(ctx, OT_EINVAL, "null result pointer");
+    int k = -1;
+    for (int i = 0; i < ot_assoc_ctx::kAsyncSlots; ++i)
+        if (ticket != 0 && ctx->async_ticket[i] == ticket) {
+            k = i;
+            break;
+        }
+    if (k < 0) return set_error(ctx, OT_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaEventSynchronize(ctx->async_ev[k][0]);
+    ctx->async_ticket[k] = 0;
+    if (e != cudaSuccess) return cuda_error(ctx, e, "asynchronous solve");
+    const SolveSummary sum = ((const SolveSummary*)ctx->async_sum)[k];
+    ctx->last_timings = ot_assoc_timings{};
+    float ms = 0.f;
+    if (ctx->timing && cudaEventElapsedTime(&ms, ctx->async_ev[k][1], ctx->async_ev[k][2]) == cudaSuccess) {
+        ctx->last_timings.loop_ms = ms;
+        ctx->last_timings.sweeps = sum.iters;
+        ctx->last_timings.valid = 1;
+    } else {
+        cudaGetLastError();
+    }
     return finish(ctx, sum, out);
 }
 

@@ -282,7 +282,7 @@ ot_status ot_assoc_adaptive(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, con
     A.outer = outer;
     A.warm = prm->cold_start ? 0 : 1;
     A.spin = ctx->spin_limit;
-    if (cudaFuncSetAttribute((const void*)sk_adaptive, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (allow_max_dynamic_smem((const void*)sk_adaptive, smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, OT_ECUDA, "adaptive kernel: %zu bytes of shared memory refused", smem);

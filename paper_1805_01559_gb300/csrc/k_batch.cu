@@ -447,7 +447,7 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
     BP.spin = ctx->spin_limit;
     b->smem = smem;
     b->grid = nsm;
-    if (cudaFuncSetAttribute((const void*)sk_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (allow_max_dynamic_smem((const void*)sk_batch, smem) !=
         cudaSuccess) {
         cudaGetLastError();
         batch_free(b);

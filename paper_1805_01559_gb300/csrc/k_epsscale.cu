@@ -197,7 +197,7 @@ ot_status ot_assoc_solve_eps_scaling(ot_assoc_ctx* ctx, const float* C, int64_t 
     A.nstages = ns;
     A.warm0 = warm_start ? 1 : 0;
     A.spin = ctx->spin_limit;
-    if (cudaFuncSetAttribute((const void*)sk_eps_scaling, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (allow_max_dynamic_smem((const void*)sk_eps_scaling, smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, OT_ECUDA, "eps-scaling kernel: %zu bytes of shared memory refused", smem);

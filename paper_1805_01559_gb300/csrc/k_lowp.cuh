@@ -535,7 +535,7 @@ ot_status lowp_solve_t(ot_assoc_ctx* ctx, const SolveArgs& a, double absorb_log2
     if (!plan_stage(nteams, I, Jp, ldk, grid, 24576, 232448 - 4096, &S, &smem, &V, (int)sizeof(T)))
         return set_error(ctx, OT_EUNSUPPORTED, "stored kernel does not fit the shared memory (I=%lld J=%d)",
                          (long long)I, J);
-    if (cudaFuncSetAttribute(kk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (allow_max_dynamic_smem(kk.fn, smem) != cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, OT_ECUDA, "stored-kernel loop: shared memory");
     }

@@ -561,7 +561,7 @@ ot_status ot_assoc_server_create(ot_assoc_ctx* ctx, const ot_assoc_server_config
     P.idle_polls = (long long)(idle / 0.3);  // a poll sleeps about 0.3 us
     P.spin = ctx->spin_limit;
     s->smem = SMEM_BUDGET;
-    if (cudaFuncSetAttribute((const void*)sk_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) !=
+    if (allow_max_dynamic_smem((const void*)sk_serve, s->smem) !=
         cudaSuccess) {
         cudaGetLastError();
         ot_assoc_server_destroy(s);

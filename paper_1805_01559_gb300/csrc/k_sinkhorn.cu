@@ -183,7 +183,52 @@ struct LoopLaunch {
     int V;
 };
 
+// Launch plans already made on this host thread (device, kernel and shape as the key): a
+// repeated solve of one shape skips the planning and the attribute and occupancy queries.
+struct PlanEntry {
+    int device = -1;
+    const void* fn = nullptr;
+    int64_t I = 0, ld = 0;
+    int Jp = 0, num_sms = 0, cap = 0;
+    LoopLaunch L;
+};
+static constexpr int PLAN_CACHE = 8;
+thread_local PlanEntry t_plans[PLAN_CACHE];
+thread_local int t_plan_next = 0;
+
+ot_status plan_solve_uncached(const Kernels& kk, int64_t I, int Jp, int64_t ld, int num_sms, int cap,
+                              LoopLaunch* L);
+
 ot_status plan_solve(const Kernels& kk, int64_t I, int Jp, int64_t ld, int num_sms, int cap, LoopLaunch* L) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return plan_solve_uncached(kk, I, Jp, ld, num_sms, cap, L);
+    }
+    for (const PlanEntry& e : t_plans)
+        if (e.fn == kk.solve && e.device == dev && e.I == I && e.Jp == Jp && e.ld == ld && e.num_sms == num_sms &&
+            e.cap == cap) {
+            *L = e.L;
+            return OT_OK;
+        }
+    const ot_status st = plan_solve_uncached(kk, I, Jp, ld, num_sms, cap, L);
+    if (st == OT_OK) {
+        PlanEntry& e = t_plans[t_plan_next];
+        t_plan_next = (t_plan_next + 1) % PLAN_CACHE;
+        e.device = dev;
+        e.fn = kk.solve;
+        e.I = I;
+        e.Jp = Jp;
+        e.ld = ld;
+        e.num_sms = num_sms;
+        e.cap = cap;
+        e.L = *L;
+    }
+    return st;
+}
+
+ot_status plan_solve_uncached(const Kernels& kk, int64_t I, int Jp, int64_t ld, int num_sms, int cap,
+                              LoopLaunch* L) {
     const int nteams = kk.ncw / kk.tw;
     const size_t budget = 232448 - 2048;  // 227 KB per block minus static shared memory
     StreamCfg S;
@@ -195,7 +240,7 @@ ot_status plan_solve(const Kernels& kk, int64_t I, int Jp, int64_t ld, int num_s
     if (!plan_stage(nteams, I, Jp, ld, grid, 24576, budget, &L->cfg, &L->smem, &L->V))
         return OT_EUNSUPPORTED;  // the rows a CTA owns do not fit next to two stages
     L->grid = grid;
-    if (cudaFuncSetAttribute(kk.solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem) != cudaSuccess) {
+    if (allow_max_dynamic_smem(kk.solve, L->smem) != cudaSuccess) {
         cudaGetLastError();
         return OT_ECUDA;
     }
@@ -241,7 +286,8 @@ __global__ void sk_set_loop(LoopState* ls, int iters, double err, int converged)
 
 // Enqueue the whole solve (or the part `mode` asks for); the caller copies B.summ back.
 cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunch& LL, const SolveBufs& B,
-                          long long spin, cudaStream_t s, ot_assoc_ctx* ctx, const SolveMode& mode = SolveMode()) {
+                          long long spin, cudaStream_t s, ot_assoc_ctx* ctx, const SolveMode& mode = SolveMode(),
+                          cudaEvent_t kev0 = nullptr, cudaEvent_t kev1 = nullptr) {
     const int J = a.J;
     const int64_t I = a.I;
     const int Jp = (int)round_up(J, 4);
@@ -284,11 +330,13 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
     P.F_in = mode.F_in;
     P.G_in = mode.G_in;
     if (ctx) timing_mark(ctx, 1, s);
+    if (kev0) cudaEventRecord(kev0, s);
     {
         void* args[] = {&P, (void*)&LL.cfg};
         e = cudaLaunchCooperativeKernel(kk.solve, dim3(LL.grid), dim3(32 * (kk.ncw + 1)), args, LL.smem, s);
         if (e != cudaSuccess) return e;
     }
+    if (kev1) cudaEventRecord(kev1, s);
     if (ctx) timing_mark(ctx, 2, s);
     if (!mode.init) {
         const int nb_cols = (int)std::max<int64_t>(1, std::min<int64_t>((J + 15) / 16, 1024));
@@ -323,7 +371,8 @@ ot_status solve_bufs(ot_assoc_ctx* ctx, const LoopLaunch& LL, int Jp, SolveBufs*
 
 }  // namespace
 
-ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* sum_host) {
+ot_status enqueue_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* dest, cudaEvent_t kev0,
+                            cudaEvent_t kev1) {
     ot_status st = OT_OK;
     const int J = a.J;
     const int64_t I = a.I;
@@ -336,16 +385,23 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
     SolveBufs B;
     st = solve_bufs(ctx, LL, Jp, &B);
     if (st) return st;
+    cudaStream_t s = a.stream;
+    cudaError_t e = enqueue_solve(a, kk, LL, B, ctx->spin_limit, s, kev0 ? nullptr : ctx, SolveMode(), kev0, kev1);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "solve launch");
+    ctx->launches += 3;
+    e = cudaMemcpyAsync(dest, B.summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "summary copy");
+    return OT_OK;
+}
+
+ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* sum_host) {
+    ot_status st = OT_OK;
     SolveSummary* hsum = (SolveSummary*)host_staging(ctx, sizeof(SolveSummary), &st);
     if (st) return st;
     ctx->last_timings.valid = 0;
-    cudaStream_t s = a.stream;
-    cudaError_t e = enqueue_solve(a, kk, LL, B, ctx->spin_limit, s, ctx);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "solve launch");
-    ctx->launches += 3;
-    e = cudaMemcpyAsync(hsum, B.summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "summary copy");
-    e = cudaStreamSynchronize(s);
+    st = enqueue_solve_f32(ctx, a, hsum, nullptr, nullptr);
+    if (st) return st;
+    cudaError_t e = cudaStreamSynchronize(a.stream);
     if (e != cudaSuccess) return cuda_error(ctx, e, "solve");
     *sum_host = *hsum;
     timing_collect(ctx, hsum->iters);

@@ -62,6 +62,12 @@ struct ot_assoc_ctx {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     ot_assoc_timings last_timings = {};
     ota::TuneEntry tune[ota::TUNE_BUCKETS];
+    // asynchronous solves: pinned summary slots, their completion and kernel events, tickets
+    static constexpr int kAsyncSlots = 16;
+    void* async_sum = nullptr;                       // pinned SolveSummary[kAsyncSlots]
+    cudaEvent_t async_ev[kAsyncSlots][3] = {};       // done, kernel start, kernel end
+    unsigned long long async_ticket[kAsyncSlots] = {};  // 0 = free
+    unsigned long long next_ticket = 1;
 };
 
 namespace ota {
@@ -109,6 +115,10 @@ struct SolveArgs {
 
 // FP32 log-domain solve (Algorithm 1).  Fills `sum_host` (synchronises).
 ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* sum_host);
+// The same solve enqueued only: the summary lands in `dest` (pinned host memory) when the
+// stream gets there; kev0/kev1 (optional) are recorded around the persistent kernel.
+ot_status enqueue_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* dest, cudaEvent_t kev0,
+                            cudaEvent_t kev1);
 
 struct SolveArgs64 {
     const double* C;
@@ -164,6 +174,12 @@ struct DeviceGuardLite {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+// Allow `fn` the largest dynamic shared memory a block may opt in to on the current device
+// (the opt-in limit minus the kernel's static shared memory); fails when `need` exceeds it.
+// The value set is the same for every call, so one launch plan never lowers the limit
+// another plan (or a captured graph) relies on.
+cudaError_t allow_max_dynamic_smem(const void* fn, size_t need);
 
 ot_status launch_maxsinr(ot_assoc_ctx* ctx, const float* R, int64_t ld_r, const float* lam,
                          int64_t I, int J, double mu, int32_t* assoc, double* Lambda,

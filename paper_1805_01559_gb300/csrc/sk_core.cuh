@@ -439,6 +439,7 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
     for (int v = 0; v < VPT; ++v) cpi[v] = crho[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     float errt = 0.f;
     const int nblk = (nrow + rs_ - 1) / rs_;
+    const bool want_pi = P.pi != nullptr;
     const int every = max(1, FIN_ROWS / S.rpt);  // stages between flushes
     const int* pend = sh->pend - v0;
     int vp = v0, vbeg = 0;
@@ -458,7 +459,7 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
             const float2 F = Fold[lr];
             const float phat = Ps[lr];
             const int64_t i = r0 + lr;
-            const float pf = P.pi ? __ldg(P.p + i) : 0.f;
+            const float pf = want_pi ? __ldg(P.p + i) : 0.f;
             float rsum = 0.f;
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
@@ -474,8 +475,12 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
                         rsum += t;
                         comp(cpi[v], c) = fmaf(phat, t, comp(cpi[v], c));
                         comp(crho[v], c) = fmaf(phat, t > 0.f ? cost * t : 0.f, comp(crho[v], c));
-                        if (P.pi && col + c < J) P.pi[i * P.pi_ld + col + c] = pf * t;
+                        comp(x, c) = t;
                     }
+                    if (want_pi)  // one uniform branch per chunk, not per cell
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (col + c < J) P.pi[i * P.pi_ld + col + c] = pf * comp(x, c);
                 }
             }
             const float2 r = team_sum_pair<TW>(rsum, sh->red, NTEAMS, tm, par);
@@ -729,15 +734,15 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                 for (int v = 0; v < VPT; ++v)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const float u = comp(x[v], c) + cst;  // log2 pi^(1/2)_ij
+                        // online (max, sum) of log2 pi^(1/2)_ij, without a branch: a divergent
+                        // branch per cell costs more than the second ex2.  The floor keeps
+                        // -inf - -inf (a column no row reaches yet) out of the exponent.
+                        const float u = comp(x[v], c) + cst;
                         float& Mc = comp(M[v], c);
                         float& Sc = comp(Sm[v], c);
-                        if (u > Mc) {
-                            Sc = fmaf(Sc, ex2(Mc - u), 1.0f);
-                            Mc = u;
-                        } else if (u > -INFINITY) {
-                            Sc += ex2(u - Mc);
-                        }
+                        const float mn = fmaxf(fmaxf(Mc, u), -1e30f);
+                        Sc = fmaf(Sc, ex2(Mc - mn), ex2(u - mn));
+                        Mc = mn;
                     }
             }
             __syncwarp();
