@@ -5,8 +5,8 @@ Workload (one "step"): the 50,000 devices x 800 RRHs instance (4 km^2, 5 hot spo
 lognormal(0, 1.5) traffic, capacity-proportional RRH marginal) with gains resident in HBM:
 rates (Sec. II-A) -> cost C = 1/(mu R) and the median of C -> three Sinkhorn solves
 (Algorithm 1, FP32 log domain, tol 1e-6, <= 2000 iterations) at eps = {0.1, 0.03, 0.01} x
-median(C), each with its FP64 finalize, enqueued back to back (asynchronous API) and waited
-for in order.  Metric: Sinkhorn cells x iterations per second
+median(C), each with its FP64 finalize, enqueued back to back through the asynchronous API
+(--multi: the three in one launch that shares each read of C, sk_solve_multi).  Metric: Sinkhorn cells x iterations per second
 over the whole step.  C (160 MB) is larger than the 126 MB L2, so no flush is needed
 between steps.
 
@@ -251,22 +251,32 @@ def run_gpu(args):
     def step(record=False):
         ctx.build_rates(G, P, inst.N0, inst.W_hz, R_out=R)
         _, med = ctx.build_cost(R, inst.mu, eps_rel=1.0, C_out=C)
-        # the three solves are enqueued back to back and waited for in order
-        pend = [ctx.solve_cost_async(C, lam, q, er * med, tol=TOL, max_iter=MAX_ITER, f=fs[k], g=gs[k])
-                for k, er in enumerate(EPS_REL)]
+        if not args.multi:
+            # the three solves enqueued back to back, each reading C on its own
+            results = [x.wait() for x in [ctx.solve_cost_async(C, lam, q, er * med, tol=TOL, max_iter=MAX_ITER,
+                                                               f=fs[k], g=gs[k]) for k, er in enumerate(EPS_REL)]]
+        else:
+            # the three solves in one launch, sharing each read of C while they iterate
+            results = ctx.solve_cost_multi(C, lam, q, [er * med for er in EPS_REL], tol=TOL, max_iter=MAX_ITER,
+                                           fs=fs, gs=gs)
         cells = 0
         its = []
-        for x in pend:
-            res = x.wait()
+        for res in results:
             cells += I * J * res.iters
             its.append(res.iters)
-            if record:
+            if record and not args.multi:
                 t = ctx.last_timings()
                 if t["valid"]:
                     # the persistent kernel reads C once per iteration, once more to test the
                     # last plan, and once in the finalize sweep
                     loop_ms.append(t["loop_ms"])
                     loop_bytes.append(4.0 * I * J * (t["sweeps"] + 2))
+        if record and args.multi:
+            t = ctx.last_timings()
+            if t["valid"]:
+                # one launch reads C max(iters) + 2 n times (timings report that as sweeps + 2)
+                loop_ms.append(t["loop_ms"])
+                loop_bytes.append(4.0 * I * J * (t["sweeps"] + 2))
         return cells, its
 
     for _ in range(args.warmup):
@@ -333,11 +343,16 @@ def run_gpu(args):
                        "iters": iters_seen[0] if iters_seen else None,
                        "l2": "inputs larger than L2 (C and G 160 MB each > 126 MB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "sk_solve (persistent Sinkhorn: setup, sweeps, finalize sweep)",
+            "roofline": {"bound": "hbm",
+                         "kernel": ("sk_solve (persistent Sinkhorn: setup, sweeps, finalize sweep), one launch per eps"
+                                    if not args.multi else
+                                    "sk_solve_multi (the three eps in one launch: first sweeps and finalize sweeps "
+                                    "one solve after the other, plan-scale sweeps shared)"),
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "peak_kind": peak_kind,
-                         "bytes_per_cell_iter": 4, "reads_of_C_per_launch": "iters + 2",
+                         "bytes_per_cell_iter": 4,
+                         "reads_of_C_per_launch": "iters + 2" if not args.multi else "max(iters) + 2 x 3",
                          "alg_bytes_per_launch": (sum(loop_bytes) / len(loop_bytes)) if loop_bytes else None,
                          "launches_timed": len(loop_ms)},
             "e2e": {"value": e2e_cells / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -795,6 +810,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--multi", action="store_true",
+                    help="c2: the three eps in one shared-read launch (slower at J = 800: see DESIGN)")
     ap.add_argument("--ref-rows", type=int, default=12_500)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="only run this many rounds of the three solves of one step (for profiler captures)")

@@ -180,6 +180,22 @@ ot_status ot_assoc_solve_cost(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, c
                               void* stream);
 
 /*
+ * Up to three solves of Algorithm 1 on ONE cost matrix (the same C, p and q, an eps sweep:
+ * eps[k], tol[k] for k < n) in one persistent launch.  Each solve follows the single-solve
+ * algorithm and stopping rule exactly; the plan-scale sweeps of the solves still iterating
+ * share each read of C, so the launch reads C max(iters) + 2 n times instead of
+ * sum(iters) + 2 n.  outs [host] n results (device pointers as for ot_assoc_solve_cost; host
+ * fields filled).  The team width is chosen for three solves' registers, so results agree
+ * with ot_assoc_solve_cost to rounding, not bit for bit.  Limits: 1 <= n <= 3, J <= 4096;
+ * one status for the launch (a solve that breaks down fails all).  Synchronises `stream`.
+ * Returns OT_OK when every solve converged, OT_NOT_CONVERGED when some stopped at max_iter.
+ */
+ot_status ot_assoc_solve_cost_multi(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* p,
+                                    const float* q, int64_t I, int64_t J, int32_t n, const double* eps,
+                                    const double* tol, int32_t max_iter, ot_assoc_result* outs,
+                                    void* stream);
+
+/*
  * ot_assoc_solve_cost without waiting: the solve is enqueued on `stream` and *ticket [host]
  * identifies it.  `out` supplies the device pointers (f, g, pi, rrh_load), which must stay
  * valid until the solve completes; ot_assoc_wait fills the host fields.  Up to 16 solves may

@@ -936,3 +936,39 @@ def _ctx_solve_cost_async(self, C, p, q, eps, tol=1e-6, max_iter=2000, warm_g=No
 
 
 Context.solve_cost_async = _ctx_solve_cost_async
+
+
+# ---- several solves on one cost matrix ----------------------------------------------------------
+SIGNATURES["ot_assoc_solve_cost_multi"] = (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _I64, _I64, _I32, _PD, _PD, _I32,
+                                                          ctypes.POINTER(ot_assoc_result), _VP])
+if _lib is not None:
+    _lib.ot_assoc_solve_cost_multi.restype, _lib.ot_assoc_solve_cost_multi.argtypes = \
+        SIGNATURES["ot_assoc_solve_cost_multi"]
+
+
+def _ctx_solve_cost_multi(self, C, p, q, eps, tol=1e-6, max_iter=2000, want_pi=False, want_load=True, fs=None,
+                          gs=None, stream=None) -> list:
+    """Up to three solves of Algorithm 1 on one C (eps sweep) in one launch; a Result each."""
+    _need(C, torch.float32, "C", 2)
+    _need(p, torch.float32, "p", 1)
+    _need(q, torch.float32, "q", 1)
+    I, J = C.shape
+    eps = [float(e) for e in eps]
+    n = len(eps)
+    tols = [float(t) for t in (tol if isinstance(tol, (list, tuple)) else [tol] * n)]
+    arr = (ot_assoc_result * max(n, 1))()
+    keep = []
+    for k in range(n):
+        r, f, g, pi, load = self._result(I, J, C.device, want_pi, want_load, fs[k] if fs else None,
+                                         gs[k] if gs else None)
+        arr[k] = r
+        keep.append((f, g, pi, load))
+    e_arr = (ctypes.c_double * max(n, 1))(*eps)
+    t_arr = (ctypes.c_double * max(n, 1))(*tols)
+    st = self._L.ot_assoc_solve_cost_multi(self._h, _ptr(C), C.stride(0), _ptr(p), _ptr(q), I, J, n, e_arr, t_arr,
+                                           int(max_iter), arr, _stream(stream))
+    self._check(st, allow_nc=True)
+    return [self._pack(arr[k], *keep[k]) for k in range(n)]
+
+
+Context.solve_cost_multi = _ctx_solve_cost_multi

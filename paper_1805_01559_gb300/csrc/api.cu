@@ -394,6 +394,46 @@ ot_status ot_assoc_solve_cost(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, c
     return finish(ctx, sum, out);
 }
 
+ot_status ot_assoc_solve_cost_multi(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* p,
+                                    const float* q, int64_t I, int64_t J, int32_t n, const double* eps,
+                                    const double* tol, int32_t max_iter, ot_assoc_result* outs, void* stream) {
+    if (!ctx) return OT_EINVAL;
+    if (!eps || !tol || !outs) return set_error(ctx, OT_EINVAL, "null eps, tol or result array");
+    if (n < 1 || n > 3) return set_error(ctx, OT_EUNSUPPORTED, "n=%d solves: 1 to 3 share one launch", n);
+    for (int k = 0; k < n; ++k) {
+        ot_status st = check_solve_args(ctx, C, p, q, I, J, ld_c, eps[k], tol[k], max_iter, &outs[k]);
+        if (st) return st;
+    }
+    if (J > 4096) return set_error(ctx, OT_EUNSUPPORTED, "J=%lld above 4096 (multi-solve)", (long long)J);
+    if (ld_c == 0) ld_c = J;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveArgs a;
+    ot_status st = aligned_view(ctx, C, ld_c, I, (int)J, s, &a.C, &a.ld);
+    if (st) return st;
+    a.p = p;
+    a.q = q;
+    a.I = I;
+    a.J = (int)J;
+    a.eps = eps[0];
+    a.tol = tol[0];
+    a.max_iter = max_iter;
+    a.warm_start = 0;
+    a.out = &outs[0];
+    a.stream = s;
+    ot_assoc_result* ptrs[3] = {&outs[0], n > 1 ? &outs[1] : nullptr, n > 2 ? &outs[2] : nullptr};
+    SolveSummary sum[3];
+    st = launch_solve_multi(ctx, a, n, eps, tol, ptrs, sum);
+    if (st) return st;
+    ot_status worst = OT_OK;
+    for (int k = 0; k < n; ++k) {
+        const ot_status sk = finish(ctx, sum[k], &outs[k]);
+        if (sk < 0 && worst >= 0) worst = sk;
+        else if (sk == OT_NOT_CONVERGED && worst == OT_OK) worst = OT_NOT_CONVERGED;
+    }
+    return worst;
+}
+
 ot_status ot_assoc_solve_cost_async(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, const float* p,
                                     const float* q, int64_t I, int64_t J, double eps, double tol, int32_t max_iter,
                                     int32_t warm_start, const ot_assoc_result* out, uint64_t* ticket,

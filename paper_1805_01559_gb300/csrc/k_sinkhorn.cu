@@ -30,10 +30,12 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "ot_common.cuh"
 #include "sk_core.cuh"
+#include "sk_multi.cuh"
 #include "ot_internal.h"
 
 namespace ota {
@@ -67,6 +69,49 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve(SolveParams P, Strea
     GroupCtx g{(int)gridDim.x, (int)blockIdx.x, &P.st->bar, 0u, &P.st->status, &P.st->status};
     int par = 0;
     sk_consumers<TW, VPT>(P, S, g, &sh, dyn, r0, r1, &par);
+}
+
+// Several solves sharing one cost matrix (sk_multi.cuh): the same launch structure.
+template <int TW, int VPT>
+__global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve_multi(MultiParams M, StreamCfg S) {
+    constexpr int NCW = Cons<TW>::NCW;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ SkShared sh;
+    uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
+    uint64_t* empty = full + MAX_STAGES;
+    float* ring = reinterpret_cast<float*>(dyn + S.off_ring);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SolveParams& P0 = M.P[0];
+    int64_t r0, r1;
+    cta_rows(P0.I, S.rows_per_stage, P0.V, blockIdx.x, gridDim.x, &r0, &r1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        sh.s_stop = 0;
+        sh.s_bad = 0;
+        sh.s_dec = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == NCW) {
+        if (lane == 0)
+            stream_rows_producer(P0.C, P0.ld, r0, r1, S, ring, full, empty, &sh.s_stop, &M.grp->status, P0.spin);
+        return;
+    }
+    GroupCtx g{(int)gridDim.x, (int)blockIdx.x, &M.grp->bar, 0u, &M.grp->status, &M.grp->status};
+    ms_consumers<TW, VPT>(M, S, g, &sh, dyn, r0, r1);
+}
+
+// The launch's status into every solve's loop state (the finalize kernels read it there).
+__global__ void sk_multi_status(const LoopState* grp, LoopState* a, LoopState* b, LoopState* c) {
+    if (threadIdx.x == 0) {
+        const int st = grp->status;
+        a->status = st;
+        if (b) b->status = st;
+        if (c) c->status = st;
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -394,6 +439,21 @@ ot_status enqueue_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary*
     return OT_OK;
 }
 
+// Kernels of the multi-solve launch: up to 4 chunks per lane (the accumulators of three
+// solves must fit the registers), so wider rows take wider teams.
+bool pick_multi(int J, Kernels* k) {
+    const int J4 = (J + 3) / 4;
+    if (J4 <= 32) *k = Kernels{(const void*)sk_solve_multi<1, 1>, 1, 1, Cons<1>::NCW};
+    else if (J4 <= 64) *k = Kernels{(const void*)sk_solve_multi<1, 2>, 1, 2, Cons<1>::NCW};
+    else if (J4 <= 96) *k = Kernels{(const void*)sk_solve_multi<1, 3>, 1, 3, Cons<1>::NCW};
+    else if (J4 <= 128) *k = Kernels{(const void*)sk_solve_multi<1, 4>, 1, 4, Cons<1>::NCW};
+    else if (J4 <= 256) *k = Kernels{(const void*)sk_solve_multi<2, 4>, 2, 4, Cons<2>::NCW};
+    else if (J4 <= 512) *k = Kernels{(const void*)sk_solve_multi<4, 4>, 4, 4, Cons<4>::NCW};
+    else if (J4 <= 1024) *k = Kernels{(const void*)sk_solve_multi<8, 4>, 8, 4, Cons<8>::NCW};
+    else return false;
+    return true;
+}
+
 ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* sum_host) {
     ot_status st = OT_OK;
     SolveSummary* hsum = (SolveSummary*)host_staging(ctx, sizeof(SolveSummary), &st);
@@ -405,6 +465,142 @@ ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* 
     if (e != cudaSuccess) return cuda_error(ctx, e, "solve");
     *sum_host = *hsum;
     timing_collect(ctx, hsum->iters);
+    return OT_OK;
+}
+
+// Several solves on one cost matrix (an eps sweep) in one launch; fills sum_host[0..n).
+ot_status launch_solve_multi(ot_assoc_ctx* ctx, const SolveArgs& a, int n, const double* eps, const double* tol,
+                             ot_assoc_result* const* outs, SolveSummary* sum_host) {
+    const int J = a.J;
+    const int64_t I = a.I;
+    const int Jp = (int)round_up(J, 4);
+    Kernels kk;
+    if (!pick_multi(J, &kk)) return set_error(ctx, OT_EUNSUPPORTED, "J=%d above 4096 (multi-solve)", J);
+    const int nteams = kk.ncw / kk.tw;
+    StreamCfg S;
+    size_t smem = 0;
+    int V = 1;
+    if (!plan_multi(nteams, n, I, Jp, a.ld, 1, 24576, (size_t)1 << 40, &S, &smem, &V))
+        return set_error(ctx, OT_EUNSUPPORTED, "multi-solve: no stage plan");
+    const int grid = std::max(1, std::min(V, ctx->num_sms));
+    if (!plan_multi(nteams, n, I, Jp, a.ld, grid, 24576, 232448 - 2048, &S, &smem, &V))
+        return set_error(ctx, OT_EUNSUPPORTED, "multi-solve: rows do not fit the shared memory (I=%lld J=%d)",
+                         (long long)I, J);
+    if (allow_max_dynamic_smem(kk.solve, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, OT_ECUDA, "multi-solve kernel: %zu bytes of shared memory refused", smem);
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk.solve, 32 * (kk.ncw + 1), smem) != cudaSuccess ||
+        occ < 1 || grid > occ * ctx->num_sms) {
+        cudaGetLastError();
+        return set_error(ctx, OT_EUNSUPPORTED, "multi-solve kernel cannot be resident");
+    }
+    // scratch: [grp state][per solve: state 4096 + cols, G, errpart, colpart, fpart]
+    auto al = [](size_t x) { return (size_t)round_up((int64_t)x, 256); };
+    const size_t st_bytes = al(4096 + sizeof(double2) * (size_t)Jp);
+    const size_t per = st_bytes + al(sizeof(double) * 3 * (size_t)Jp) + al(sizeof(double) * 2 * (size_t)V) +
+                       al(sizeof(float2) * (size_t)V * Jp) + al(sizeof(double2) * (size_t)V * Jp);
+    ot_status st = OT_OK;
+    char* base = (char*)scratch(ctx, SLOT_MISC, 256 + per * n, &st);
+    if (st) return st;
+    SolveSummary* hsum = (SolveSummary*)host_staging(ctx, sizeof(SolveSummary) * n, &st);
+    if (st) return st;
+    MultiParams M;
+    std::memset(&M, 0, sizeof(M));
+    M.n = n;
+    M.grp = (LoopState*)base;
+    struct Bufs {
+        DevScalars* sc;
+        LoopState* ls;
+        SolveSummary* summ;
+        double2* cols;
+        double* G;
+        double* errpart;
+        float* colpart;
+        double2* fpart;
+    } B[MS_MAX];
+    cudaStream_t s = a.stream;
+    cudaError_t e = cudaMemsetAsync(base, 0, 256, s);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        char* q = base + 256 + per * k;
+        e = cudaMemsetAsync(q, 0, 1024, s);
+        B[k].sc = (DevScalars*)q;
+        B[k].ls = (LoopState*)(q + 256);
+        B[k].summ = (SolveSummary*)(q + 512);
+        B[k].cols = (double2*)(q + 4096);
+        size_t o = st_bytes;
+        B[k].G = (double*)(q + o);
+        o += al(sizeof(double) * 3 * (size_t)Jp);
+        B[k].errpart = (double*)(q + o);
+        o += al(sizeof(double) * 2 * (size_t)V);
+        B[k].colpart = (float*)(q + o);
+        o += al(sizeof(float2) * (size_t)V * Jp);
+        B[k].fpart = (double2*)(q + o);
+        SolveParams& P = M.P[k];
+        const double kk2 = LOG2E / eps[k];
+        P.C = a.C;
+        P.ld = a.ld;
+        P.I = I;
+        P.J = J;
+        P.Jp = Jp;
+        P.V = V;
+        P.p = a.p;
+        P.q = a.q;
+        P.g_warm = nullptr;
+        P.input_bad = a.input_bad;
+        P.sc = B[k].sc;
+        P.st = B[k].ls;
+        P.G = B[k].G;
+        P.F_out = nullptr;
+        P.colpart = B[k].colpart;
+        P.errpart = k == 0 ? B[0].errpart : B[k].errpart;
+        P.k = kk2;
+        split_k(kk2, &P.k_hi, &P.k_lo);
+        P.tol = tol[k];
+        P.max_iter = a.max_iter;
+        P.spin = ctx->spin_limit;
+        P.fpart = B[k].fpart;
+        P.epart = B[k].errpart + V;
+        P.pi = outs[k]->pi;
+        P.pi_ld = outs[k]->pi_ld > 0 ? outs[k]->pi_ld : J;
+        P.f_nat = outs[k]->f;
+        P.eps_ln2 = eps[k] * LN2;
+        P.F_in = nullptr;
+        P.G_in = nullptr;
+    }
+    if (e != cudaSuccess) return cuda_error(ctx, e, "multi-solve memset");
+    ctx->last_timings.valid = 0;
+    timing_mark(ctx, 0, s);
+    timing_mark(ctx, 1, s);
+    {
+        void* args[] = {&M, &S};
+        e = cudaLaunchCooperativeKernel(kk.solve, dim3(grid), dim3(32 * (kk.ncw + 1)), args, smem, s);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "multi-solve launch");
+    }
+    timing_mark(ctx, 2, s);
+    sk_multi_status<<<1, 32, 0, s>>>(M.grp, B[0].ls, n > 1 ? B[1].ls : nullptr, n > 2 ? B[2].ls : nullptr);
+    const int nb_cols = (int)std::max<int64_t>(1, std::min<int64_t>((J + 15) / 16, 1024));
+    for (int k = 0; k < n; ++k) {
+        sk_finalize_cols<<<nb_cols, 512, 0, s>>>(B[k].fpart, V, Jp, J, a.q, B[k].sc, B[k].ls, B[k].G, 1,
+                                                 eps[k] * LN2, outs[k]->g, outs[k]->rrh_load, B[k].cols);
+        sk_summary<<<1, 256, 0, s>>>(B[k].errpart + V, V, B[k].cols, J, B[k].sc, B[k].ls, B[k].summ);
+    }
+    timing_mark(ctx, 3, s);
+    ctx->launches += 2 + 2 * n;
+    e = cudaGetLastError();
+    for (int k = 0; k < n && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(hsum + k, B[k].summ, sizeof(SolveSummary), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "multi-solve");
+    int mx = 0;
+    for (int k = 0; k < n; ++k) {
+        sum_host[k] = hsum[k];
+        mx = std::max(mx, hsum[k].iters);
+    }
+    // the launch reads C once per fused sweep (max iters of the solves) and twice per solve
+    // (its first iteration and its finalize sweep): sweeps + 2 = max iters + 2 n
+    timing_collect(ctx, mx + 2 * n - 2);
     return OT_OK;
 }
 

@@ -115,6 +115,9 @@ struct SolveArgs {
 
 // FP32 log-domain solve (Algorithm 1).  Fills `sum_host` (synchronises).
 ot_status launch_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* sum_host);
+// Up to three solves on one cost matrix (same p, q; eps[k], tol[k]) in one launch.
+ot_status launch_solve_multi(ot_assoc_ctx* ctx, const SolveArgs& a, int n, const double* eps, const double* tol,
+                             ot_assoc_result* const* outs, SolveSummary* sum_host);
 // The same solve enqueued only: the summary lands in `dest` (pinned host memory) when the
 // stream gets there; kev0/kev1 (optional) are recorded around the persistent kernel.
 ot_status enqueue_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary* dest, cudaEvent_t kev0,
