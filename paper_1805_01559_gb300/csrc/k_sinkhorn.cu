@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve(SolveParams P, Strea
 }
 
 // Several solves sharing one cost matrix (sk_multi.cuh): the same launch structure.
-template <int TW, int VPT>
+template <int TW, int VPT, int NS, bool RC>
 __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve_multi(MultiParams M, StreamCfg S) {
     constexpr int NCW = Cons<TW>::NCW;
     extern __shared__ __align__(128) unsigned char dyn[];
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve_multi(MultiParams M,
         return;
     }
     GroupCtx g{(int)gridDim.x, (int)blockIdx.x, &M.grp->bar, 0u, &M.grp->status, &M.grp->status};
-    ms_consumers<TW, VPT>(M, S, g, &sh, dyn, r0, r1);
+    ms_consumers<TW, VPT, NS, RC>(M, S, g, &sh, dyn, r0, r1);
 }
 
 // The launch's status into every solve's loop state (the finalize kernels read it there).
@@ -439,17 +439,27 @@ ot_status enqueue_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary*
     return OT_OK;
 }
 
-// Kernels of the multi-solve launch: up to 4 chunks per lane (the accumulators of three
-// solves must fit the registers), so wider rows take wider teams.
-bool pick_multi(int J, Kernels* k) {
+// Kernels of the multi-solve launch.  Up to 128 float4 chunks a row, one-warp teams keep
+// three solves' accumulators with the row (4 chunks a lane).  Wider rows: two solves on
+// one-warp teams with the cell values computed twice (the row stays with the one-warp
+// team of a single solve), three solves on wider teams (4 chunks a lane).
+template <int TW, int VPT, int NS, bool RC>
+Kernels multi_for() {
+    return Kernels{(const void*)sk_solve_multi<TW, VPT, NS, RC>, TW, VPT, Cons<TW>::NCW};
+}
+bool pick_multi(int J, int n, Kernels* k) {
     const int J4 = (J + 3) / 4;
-    if (J4 <= 32) *k = Kernels{(const void*)sk_solve_multi<1, 1>, 1, 1, Cons<1>::NCW};
-    else if (J4 <= 64) *k = Kernels{(const void*)sk_solve_multi<1, 2>, 1, 2, Cons<1>::NCW};
-    else if (J4 <= 96) *k = Kernels{(const void*)sk_solve_multi<1, 3>, 1, 3, Cons<1>::NCW};
-    else if (J4 <= 128) *k = Kernels{(const void*)sk_solve_multi<1, 4>, 1, 4, Cons<1>::NCW};
-    else if (J4 <= 256) *k = Kernels{(const void*)sk_solve_multi<2, 4>, 2, 4, Cons<2>::NCW};
-    else if (J4 <= 512) *k = Kernels{(const void*)sk_solve_multi<4, 4>, 4, 4, Cons<4>::NCW};
-    else if (J4 <= 1024) *k = Kernels{(const void*)sk_solve_multi<8, 4>, 8, 4, Cons<8>::NCW};
+    if (J4 <= 32) *k = multi_for<1, 1, 3, false>();
+    else if (J4 <= 64) *k = multi_for<1, 2, 3, false>();
+    else if (J4 <= 96) *k = multi_for<1, 3, 3, false>();
+    else if (J4 <= 128) *k = multi_for<1, 4, 3, false>();
+    else if (n <= 2 && J4 <= 160) *k = multi_for<1, 5, 2, true>();
+    else if (n <= 2 && J4 <= 192) *k = multi_for<1, 6, 2, true>();
+    else if (n <= 2 && J4 <= 224) *k = multi_for<1, 7, 2, true>();
+    else if (n <= 2 && J4 <= 256) *k = multi_for<1, 8, 2, true>();
+    else if (J4 <= 256) *k = multi_for<2, 4, 3, false>();
+    else if (J4 <= 512) *k = multi_for<4, 4, 3, false>();
+    else if (J4 <= 1024) *k = multi_for<8, 4, 3, false>();
     else return false;
     return true;
 }
@@ -475,7 +485,7 @@ ot_status launch_solve_multi(ot_assoc_ctx* ctx, const SolveArgs& a, int n, const
     const int64_t I = a.I;
     const int Jp = (int)round_up(J, 4);
     Kernels kk;
-    if (!pick_multi(J, &kk)) return set_error(ctx, OT_EUNSUPPORTED, "J=%d above 4096 (multi-solve)", J);
+    if (!pick_multi(J, n, &kk)) return set_error(ctx, OT_EUNSUPPORTED, "J=%d above 4096 (multi-solve)", J);
     const int nteams = kk.ncw / kk.tw;
     StreamCfg S;
     size_t smem = 0;

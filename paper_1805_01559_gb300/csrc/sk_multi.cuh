@@ -262,7 +262,10 @@ __device__ __forceinline__ bool ms_first_sweep(const SolveParams& P, const Strea
 
 // The consumer warps of a multi-solve launch.  ret_par[s] receives the row potential buffer
 // of solve s's returned plan.  Returns false when the launch failed (status set).
-template <int TW, int VPT>
+// NS: solves the fused sweeps can hold (accumulator registers); RC: the cell values of a row
+// are computed twice per solve (once for the row sum, once for the column partials) instead
+// of being kept, which frees a row's worth of registers for wide rows at one more ex2 a cell.
+template <int TW, int VPT, int NS, bool RC>
 __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamCfg& S, GroupCtx& g, SkShared* sh,
                                              unsigned char* dyn, int64_t r0, int64_t r1) {
     constexpr int NCW = Cons<TW>::NCW;
@@ -406,10 +409,10 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
     unsigned active = (1u << n) - 1u;
     int retp[MS_MAX] = {0, 0, 0};
     for (int it = 2;; ++it) {
-        float4 acc[MS_MAX][VPT];
-        float errt[MS_MAX];
+        float4 acc[NS][VPT];
+        float errt[NS];
 #pragma unroll
-        for (int s = 0; s < MS_MAX; ++s) {
+        for (int s = 0; s < NS; ++s) {
             errt[s] = 0.f;
 #pragma unroll
             for (int v = 0; v < VPT; ++v) acc[s][v] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -431,8 +434,61 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
                     float4 x[VPT];
                     load_row_smem<TW, VPT>(stage + (size_t)rr * P0.ld, J, tm.tl, x);
                     const float ph_ = Ps[lr];
+                    if constexpr (RC) {
+                        float dd[NS];
+                        float2 FF[NS];
 #pragma unroll
-                    for (int s = 0; s < MS_MAX; ++s) {
+                        for (int s = 0; s < NS; ++s) {
+                            dd[s] = 0.f;
+                            FF[s] = make_float2(0.f, 0.f);
+                            if (!((active >> s) & 1u)) continue;
+                            const SolveParams& P = M.P[s];
+                            const float* Gs = Gbase + (size_t)s * Jp;
+                            const float2* Fold = Fbase + (size_t)s * 2 * S.rmax + ((it - 1) & 1) * S.rmax;
+                            float2* Fnew = Fbase + (size_t)s * 2 * S.rmax + (it & 1) * S.rmax;
+                            const float2 F = Fold[lr];
+                            FF[s] = F;
+                            float rsum = 0.f;
+#pragma unroll
+                            for (int v = 0; v < VPT; ++v) {
+                                const int col = 4 * (tm.tl + TT * v);
+                                if (chunk_inside<TW, VPT>(v) || col < J) {
+                                    float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+#pragma unroll
+                                    for (int c = 0; c < 4; ++c)
+                                        rsum += ex2(expo(F.x, F.y + comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
+                                }
+                            }
+                            rsum = team_reduce<TW, float, false>(rsum, red, NTEAMS, tm, par);
+                            const float2 Fn = df_sub(F, log2_corr(rsum));
+                            if (tm.tl == 0) Fnew[lr] = Fn;
+                            errt[s] = fmaf(ph_, fabsf(rsum - 1.0f), errt[s]);
+                            dd[s] = __fdividef(ph_, rsum);
+                        }
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) {
+                            if (!((active >> s) & 1u)) continue;
+                            const SolveParams& P = M.P[s];
+                            const float* Gs = Gbase + (size_t)s * Jp;
+                            const float2 F = FF[s];
+                            const float d = dd[s];
+#pragma unroll
+                            for (int v = 0; v < VPT; ++v) {
+                                const int col = 4 * (tm.tl + TT * v);
+                                if (chunk_inside<TW, VPT>(v) || col < J) {
+                                    float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+#pragma unroll
+                                    for (int c = 0; c < 4; ++c) {
+                                        const float t = ex2(expo(F.x, F.y + comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
+                                        comp(acc[s][v], c) = fmaf(t, d, comp(acc[s][v], c));
+                                    }
+                                }
+                            }
+                        }
+                        continue;
+                    }
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
                         if (!((active >> s) & 1u)) continue;  // uniform over the launch
                         const SolveParams& P = M.P[s];
                         const float* Gs = Gbase + (size_t)s * Jp;
@@ -476,7 +532,7 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
             }
             // end of partition vp: each active solve's column partials and row residual
 #pragma unroll
-            for (int s = 0; s < MS_MAX; ++s) {
+            for (int s = 0; s < NS; ++s) {
                 if (!((active >> s) & 1u)) continue;
                 const SolveParams& P = M.P[s];
                 if (tm.tl == 0) errf[tm.team] = errt[s];
