@@ -3,7 +3,7 @@
 
 Workload (one "step"): the 50,000 devices x 800 RRHs instance (4 km^2, 5 hot spots,
 lognormal(0, 1.5) traffic, capacity-proportional RRH marginal) with gains resident in HBM:
-rates (Sec. II-A) -> cost C = 1/(mu R) and the median of C -> three Sinkhorn solves
+rates (Sec. II-A) and cost C = 1/(mu R) in one pass, the median of C -> three Sinkhorn solves
 (Algorithm 1, FP32 log domain, tol 1e-6, <= 2000 iterations) at eps = {0.1, 0.03, 0.01} x
 median(C), each with its FP64 finalize, enqueued back to back through the asynchronous API
 (--multi: the two smaller eps in one launch that shares each read of C, sk_solve_multi).  Metric: Sinkhorn cells x iterations per second
@@ -239,7 +239,6 @@ def run_gpu(args):
     P = P_h.to(dev)
     lam = lam_h.to(dev)
     q = q_h.to(dev)
-    R = torch.empty((I, J), dtype=torch.float32, device=dev)
     C = torch.empty((I, J), dtype=torch.float32, device=dev)
     fs = [torch.empty(I, dtype=torch.float64, device=dev) for _ in EPS_REL]
     gs = [torch.empty(J, dtype=torch.float64, device=dev) for _ in EPS_REL]
@@ -249,8 +248,8 @@ def run_gpu(args):
     iters_seen = []
 
     def step(record=False):
-        ctx.build_rates(G, P, inst.N0, inst.W_hz, R_out=R)
-        _, med = ctx.build_cost(R, inst.mu, eps_rel=1.0, C_out=C)
+        # rates (Sec. II-A) and the cost in one pass over the gains, then the median of C
+        _, med = ctx.build_cost_from_gains(G, P, inst.N0, inst.W_hz, inst.mu, eps_rel=1.0, C_out=C)
         if not args.multi:
             # the three solves enqueued back to back, each reading C on its own
             results = [x.wait() for x in [ctx.solve_cost_async(C, lam, q, er * med, tol=TOL, max_iter=MAX_ITER,
@@ -812,6 +811,75 @@ def run_policies(args):
     return 0
 
 
+def run_euclid(args):
+    """The Euclidean cost of Sec. IV (cost choice (i)) on the 50,000 x 800 geometry: Algorithm 1
+    with C formed inside every sweep from the coordinates (no matrix read), at eps = {0.1,
+    0.03, 0.01} x median(C); against the same solves on the materialized matrix."""
+    import torch
+
+    from paper_1805_01559_gb300 import binding, instances as ins
+    inst = ins.make_instance("c2_50000x800", 50_000, 800, 2000.0, 0, hotspot=True, traffic_sigma=1.5,
+                             marginal="capacity", eps_rel=EPS_REL, dtype=np.float32, keep_geometry=True)
+    I, J = inst.I, inst.J
+    dev = torch.device("cuda", 0)
+    ctx = binding.Context(0)
+    dxy = torch.from_numpy(np.ascontiguousarray(inst.dev_xy, np.float32)).to(dev)
+    rxy = torch.from_numpy(np.ascontiguousarray(inst.rrh_xy, np.float32)).to(dev)
+    lam = torch.from_numpy(inst.lam.astype(np.float32)).to(dev)
+    q = torch.from_numpy(inst.q.astype(np.float32)).to(dev)
+    C = ctx.euclid_cost(dxy, rxy)
+    med = ctx.median_f32(C.contiguous().view(-1))
+    s = torch.cuda.current_stream()
+
+    def fly():
+        return [ctx.solve_euclid(dxy, rxy, lam, q, er * med, tol=TOL, max_iter=MAX_ITER).iters for er in EPS_REL]
+
+    def mat():
+        return [ctx.solve_cost(C, lam, q, er * med, tol=TOL, max_iter=MAX_ITER).iters for er in EPS_REL]
+
+    for _ in range(args.warmup):
+        fly()
+        mat()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = ctx.launch_count()
+    ms_f = []
+    its = None
+    for _ in range(args.steps):
+        its, ms, _ = _timed(fly, s)
+        ms_f.append(ms)
+    launches = (ctx.launch_count() - l0) / args.steps
+    clk = clocks.stop()
+    ms_m = []
+    its_m = None
+    for _ in range(max(1, args.steps // 2)):
+        its_m, ms, _ = _timed(mat, s)
+        ms_m.append(ms)
+    ms = statistics.median(ms_f)
+    ci = float(I) * J * sum(its)
+    # two SFU operations a cell and sweep (the exponential and the square root's reciprocal
+    # square root): 152 SMs x 16 SFU results a clock x 2.07 GHz / 2
+    peak_cells = 152 * 16 * 2.07e9 / 2
+    sweeps = sum(it + 2 for it in its)
+    achieved = float(I) * J * sweeps / (ms / 1e3)
+    line = {"metric": METRIC, "value": ci / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "euclid_50000x800: Sinkhorn with C_ij = |x_i - x_j| formed in the sweep, "
+                                   "eps = {0.1,0.03,0.01} x median(C)", "I": I, "J": J, "iters": its, "tol": TOL,
+                       "l2": "no matrix is read"},
+            "materialized": {"ms": statistics.median(ms_m), "iters": its_m,
+                             "cells_iters_per_s": float(I) * J * sum(its_m) / (statistics.median(ms_m) / 1e3)},
+            "roofline": {"bound": "alu", "kernel": "sk_solve_euclid (SFU: ex2 and the square root per cell)",
+                         "achieved": achieved, "peak": peak_cells, "unit": "cells*sweeps/s",
+                         "frac": achieved / peak_cells, "traffic": None,
+                         "peak_kind": "derived: 152 SMs x 16 SFU/clk x 2.07 GHz / 2 SFU ops per cell"},
+            "gpu_launches": launches, "clocks": clk}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -824,7 +892,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=12_500)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="only run this many rounds of the three solves of one step (for profiler captures)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2", "policies"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2", "policies", "euclid"],
                     help="c2: the headline line; c3 batched ragged; c4 stored-kernel precision; c5 serving; "
                          "alg2 adaptive association (Algorithm 2)")
     ap.add_argument("--alg2-outer", type=int, default=20)
@@ -840,7 +908,7 @@ def main():
         return run_profile_solve(args)
     if args.workload != "c2" and args.impl != "reference":
         return {"c3": run_c3, "c4": run_c4, "c5": run_c5, "alg2": run_alg2,
-                "policies": run_policies}[args.workload](args)
+                "policies": run_policies, "euclid": run_euclid}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

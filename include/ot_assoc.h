@@ -116,6 +116,18 @@ ot_status ot_assoc_build_cost(ot_assoc_ctx* ctx, const float* R, int64_t ld_r, i
                               double* eps_out, void* stream);
 
 /*
+ * Rates and cost in one pass over the gains (Sec. II-A then Sec. IV choice (ii)): the same
+ * values as ot_assoc_build_rates followed by ot_assoc_build_cost, without writing and
+ * re-reading R.  R_out [device] (ld_r) may be NULL; C_out [device] float I x J (ld_c);
+ * eps_out / eps_rel as ot_assoc_build_cost (the median synchronises the stream; invalid
+ * rates are reported then as OT_EINVAL).  G 16-byte aligned rows are read in place.
+ */
+ot_status ot_assoc_build_cost_from_gains(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const float* P,
+                                         int64_t I, int64_t J, double N0, double W_hz, double mu,
+                                         float* R_out, int64_t ld_r, float* C_out, int64_t ld_c,
+                                         double eps_rel, double* eps_out, void* stream);
+
+/*
  * Exact median of n floats (no NaN): the middle order statistic, or the mean of
  * the two middle ones for even n.  x [device]; *median_out [host].  Synchronises.
  */
@@ -178,6 +190,20 @@ ot_status ot_assoc_solve_cost(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, c
                               const float* q, int64_t I, int64_t J, double eps, double tol,
                               int32_t max_iter, int32_t warm_start, ot_assoc_result* out,
                               void* stream);
+
+/*
+ * Algorithm 1 with the Euclidean cost of Sec. IV (cost choice (i)), C_ij = ||x_i - x_j||,
+ * formed inside every sweep from the coordinates instead of read from a matrix: no I x J
+ * array exists, each cell costs a square root and an exponential.  C_ij is evaluated in
+ * FP32 as sqrt((x_i - x_j)^2 + (y_i - y_j)^2) with every operation correctly rounded and
+ * none fused, so a solve on a matrix built with that formula gives the same result.
+ *   dev_xy [device] float I x 2 (x, y per device), rrh_xy [device] float J x 2, 8-byte aligned.
+ * Other arguments and results as ot_assoc_solve_cost (rrh_load and the transport cost are
+ * those of the Euclidean cost).  Synchronises `stream`.
+ */
+ot_status ot_assoc_solve_euclid(ot_assoc_ctx* ctx, const float* dev_xy, const float* rrh_xy, const float* p,
+                                const float* q, int64_t I, int64_t J, double eps, double tol,
+                                int32_t max_iter, int32_t warm_start, ot_assoc_result* out, void* stream);
 
 /*
  * Up to three solves of Algorithm 1 on ONE cost matrix (the same C, p and q, an eps sweep:

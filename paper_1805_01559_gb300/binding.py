@@ -972,3 +972,61 @@ def _ctx_solve_cost_multi(self, C, p, q, eps, tol=1e-6, max_iter=2000, want_pi=F
 
 
 Context.solve_cost_multi = _ctx_solve_cost_multi
+
+
+# ---- Euclidean cost formed inside the sweeps -------------------------------------------------------
+SIGNATURES["ot_assoc_solve_euclid"] = (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I64, _I64, _D, _D, _I32, _I32,
+                                                      ctypes.POINTER(ot_assoc_result), _VP])
+if _lib is not None:
+    _lib.ot_assoc_solve_euclid.restype, _lib.ot_assoc_solve_euclid.argtypes = SIGNATURES["ot_assoc_solve_euclid"]
+
+
+def _ctx_solve_euclid(self, dev_xy, rrh_xy, p, q, eps, tol=1e-6, max_iter=2000, warm_g=None, want_pi=False,
+                      want_load=True, stream=None) -> Result:
+    """Algorithm 1 with C_ij = ||x_i - x_j|| formed on the fly (no cost matrix)."""
+    _need(dev_xy, torch.float32, "dev_xy", 2)
+    _need(rrh_xy, torch.float32, "rrh_xy", 2)
+    _need(p, torch.float32, "p", 1)
+    _need(q, torch.float32, "q", 1)
+    if not dev_xy.is_contiguous() or not rrh_xy.is_contiguous() or dev_xy.shape[1] != 2 or rrh_xy.shape[1] != 2:
+        raise ValueError("coordinates must be contiguous (n, 2) tensors")
+    I, J = dev_xy.shape[0], rrh_xy.shape[0]
+    g = warm_g.clone() if warm_g is not None else None
+    r, f, g, pi, load = self._result(I, J, dev_xy.device, want_pi, want_load, None, g)
+    st = self._L.ot_assoc_solve_euclid(self._h, _ptr(dev_xy), _ptr(rrh_xy), _ptr(p), _ptr(q), I, J, float(eps),
+                                       float(tol), int(max_iter), int(warm_g is not None), ctypes.byref(r),
+                                       _stream(stream))
+    self._check(st, allow_nc=True)
+    return self._pack(r, f, g, pi, load)
+
+
+Context.solve_euclid = _ctx_solve_euclid
+
+
+# ---- rates and cost in one pass --------------------------------------------------------------------
+SIGNATURES["ot_assoc_build_cost_from_gains"] = (ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _I64, _D, _D, _D, _VP,
+                                                               _I64, _VP, _I64, _D, _PD, _VP])
+if _lib is not None:
+    _lib.ot_assoc_build_cost_from_gains.restype, _lib.ot_assoc_build_cost_from_gains.argtypes = \
+        SIGNATURES["ot_assoc_build_cost_from_gains"]
+
+
+def _ctx_build_cost_from_gains(self, G, P, N0, W_hz, mu, eps_rel=None, C_out=None, R_out=None, stream=None):
+    """Rates (Sec. II-A) and cost 1/(mu R) in one pass over the gains; returns (C, eps or None)."""
+    _need(G, torch.float32, "G", 2)
+    _need(P, torch.float32, "P", 1)
+    I, J = G.shape
+    if C_out is None:
+        C_out = torch.empty((I, J), dtype=torch.float32, device=G.device)
+    _need(C_out, torch.float32, "C_out", 2)
+    if R_out is not None:
+        _need(R_out, torch.float32, "R_out", 2)
+    eps = ctypes.c_double(0.0)
+    self._check(self._L.ot_assoc_build_cost_from_gains(
+        self._h, _ptr(G), G.stride(0), _ptr(P), I, J, float(N0), float(W_hz), float(mu), _ptr(R_out),
+        R_out.stride(0) if R_out is not None else 0, _ptr(C_out), C_out.stride(0), float(eps_rel or 0.0),
+        ctypes.byref(eps) if eps_rel is not None else None, _stream(stream)))
+    return C_out, (eps.value if eps_rel is not None else None)
+
+
+Context.build_cost_from_gains = _ctx_build_cost_from_gains

@@ -260,6 +260,50 @@ void ot_assoc_set_spin_limit(ot_assoc_ctx* ctx, int64_t polls) {
     if (ctx) ctx->spin_limit = polls >= 1 ? polls : (1LL << 24);
 }
 
+ot_status ot_assoc_build_cost_from_gains(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const float* P,
+                                         int64_t I, int64_t J, double N0, double W_hz, double mu, float* R_out,
+                                         int64_t ld_r, float* C_out, int64_t ld_c, double eps_rel, double* eps_out,
+                                         void* stream) {
+    if (!ctx) return OT_EINVAL;
+    if (!G || !P || !C_out) return set_error(ctx, OT_EINVAL, "null pointer");
+    if (I <= 0 || J <= 0) return set_error(ctx, OT_EINVAL, "I and J must be positive");
+    if (J > 8192) return set_error(ctx, OT_EUNSUPPORTED, "J above 8192");
+    if (ld_g == 0) ld_g = J;
+    if (ld_r == 0) ld_r = J;
+    if (ld_c == 0) ld_c = J;
+    if (ld_g < J || ld_r < J || ld_c < J) return set_error(ctx, OT_EINVAL, "leading dimension < J");
+    if (!(N0 >= 0.0) || !(W_hz > 0.0)) return set_error(ctx, OT_EINVAL, "need N0 >= 0 and W_hz > 0");
+    if (!(mu > 0.0) || !std::isfinite(mu)) return set_error(ctx, OT_EINVAL, "mu must be finite and > 0");
+    if (eps_out && !(eps_rel > 0.0)) return set_error(ctx, OT_EINVAL, "eps_rel must be > 0");
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    ot_status st = aligned_view(ctx, G, ld_g, I, (int)J, s, &G, &ld_g, SLOT_ALIGN);
+    if (st) return st;
+    char* state = (char*)scratch(ctx, SLOT_MISC, 256, &st);
+    if (st) return st;
+    unsigned long long* bad = (unsigned long long*)state;
+    double* med = (double*)(state + 64);
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "memset");
+    st = launch_rates(ctx, G, ld_g, P, I, (int)J, N0, W_hz, R_out, ld_r, s, mu, C_out, ld_c, bad);
+    if (st) return st;
+    if (!eps_out) return OT_OK;
+    st = launch_median(ctx, C_out, I, J, ld_c, med, s);
+    if (st) return st;
+    struct {
+        unsigned long long bad;
+        double med;
+    }* h = (decltype(h))host_staging(ctx, 64, &st);
+    if (st) return st;
+    e = cudaMemcpyAsync(&h->bad, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h->med, med, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "build_cost_from_gains");
+    if (h->bad) return set_error(ctx, OT_EINVAL, "%llu rate entries are not finite and > 0", h->bad);
+    *eps_out = eps_rel * h->med;
+    return OT_OK;
+}
+
 ot_status ot_assoc_build_rates(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const float* P, int64_t I,
                                int64_t J, double N0, double W_hz, float* R_out, int64_t ld_r, void* stream) {
     if (!ctx) return OT_EINVAL;
@@ -388,6 +432,37 @@ ot_status ot_assoc_solve_cost(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, c
     a.warm_start = warm_start;
     a.out = out;
     a.stream = s;
+    SolveSummary sum;
+    st = launch_solve_f32(ctx, a, &sum);
+    if (st) return st;
+    return finish(ctx, sum, out);
+}
+
+ot_status ot_assoc_solve_euclid(ot_assoc_ctx* ctx, const float* dev_xy, const float* rrh_xy, const float* p,
+                                const float* q, int64_t I, int64_t J, double eps, double tol, int32_t max_iter,
+                                int32_t warm_start, ot_assoc_result* out, void* stream) {
+    if (!ctx) return OT_EINVAL;
+    if (!dev_xy || !rrh_xy) return set_error(ctx, OT_EINVAL, "null coordinates");
+    if (((uintptr_t)dev_xy & 7u) || ((uintptr_t)rrh_xy & 7u))
+        return set_error(ctx, OT_EINVAL, "coordinates must be 8-byte aligned (x, y float pairs)");
+    ot_status st = check_solve_args(ctx, dev_xy, p, q, I, J, 0, eps, tol, max_iter, out);
+    if (st) return st;
+    DeviceGuard g(ctx->device);
+    SolveArgs a;
+    a.C = nullptr;
+    a.ld = round_up(J, 4);
+    a.p = p;
+    a.q = q;
+    a.I = I;
+    a.J = (int)J;
+    a.eps = eps;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.warm_start = warm_start;
+    a.out = out;
+    a.stream = (cudaStream_t)stream;
+    a.dev_xy = (const float2*)dev_xy;
+    a.rrh_xy = (const float2*)rrh_xy;
     SolveSummary sum;
     st = launch_solve_f32(ctx, a, &sum);
     if (st) return st;

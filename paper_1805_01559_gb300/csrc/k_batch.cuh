@@ -119,25 +119,36 @@ __device__ __forceinline__ bool bt_finalize(const BInst& D, const SolveParams& P
 // One instance on this CTA's group: (re)arm the stage barriers, stream and sweep, finalize.
 // Returns false when the launch must end (a wait gave up).
 template <int VPT>
-__device__ __forceinline__ bool bt_instance(const BInst& D, BRes* out, int* abort, long long spin, const BGroup& grp,
+__device__ __noinline__ bool bt_instance(const BInst& D, BRes* out, int* abort, long long spin, const BGroup& grp,
                                             int rank, int gsize, unsigned* gbar, unsigned* s_gen, int* s_nbar,
                                             SkShared* sh, unsigned char* dyn) {
-    SolveParams P = D.P;
-    P.sc = grp.sc;
-    P.st = grp.ls;
-    P.G = grp.G;
-    P.colpart = grp.colpart;
-    P.errpart = grp.errpart;
-    P.F_out = nullptr;
-    P.spin = spin;
-    P.fpart = grp.fpart;
-    P.epart = grp.fred + (size_t)gsize * BT_NW * 2;
-    P.pi = D.pi;
-    P.pi_ld = D.pi_ld;
-    P.f_nat = D.f_out;
-    P.eps_ln2 = D.eps_ln2;
-    P.F_in = nullptr;
-    P.G_in = nullptr;
+    // the instance's parameters with the group's scratch, in shared memory: the solver reads
+    // its fields from there as a single-instance kernel reads its parameter block, instead of
+    // holding a copy in registers
+    __shared__ SolveParams s_P;
+    if (threadIdx.x == 0) {
+        SolveParams P = D.P;
+        P.sc = grp.sc;
+        P.st = grp.ls;
+        P.G = grp.G;
+        P.colpart = grp.colpart;
+        P.errpart = grp.errpart;
+        P.F_out = nullptr;
+        P.spin = spin;
+        P.fpart = grp.fpart;
+        P.epart = grp.fred + (size_t)gsize * BT_NW * 2;
+        P.pi = D.pi;
+        P.pi_ld = D.pi_ld;
+        P.f_nat = D.f_out;
+        P.eps_ln2 = D.eps_ln2;
+        P.F_in = nullptr;
+        P.G_in = nullptr;
+        P.dev_xy = nullptr;
+        P.rrh_xy = nullptr;
+        s_P = P;
+    }
+    __syncthreads();
+    const SolveParams& P = s_P;
     const StreamCfg S = D.S;
     uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
     uint64_t* empty = full + MAX_STAGES;

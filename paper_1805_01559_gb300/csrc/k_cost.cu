@@ -31,11 +31,15 @@ static constexpr int NTC = 256;
 // as error-free FP32 pairs (no FP64: GB300 issues it at a small fraction of the FP32 rate).  Each own term P_j G_ij is kept as an exact hi + lo pair, so
 // T_i - own loses nothing when one RRH dominates (T_hi - own_hi is exact by Sterbenz).
 // ------------------------------------------------------------------------------------------
+// With C non-null the same pass also writes the cost C_ij = (1/mu) / R_ij (one IEEE FP32
+// division, as k_cost) and counts rates that are not finite and > 0; R may then be null.
 template <int TW, int VPT>
 __global__ void __launch_bounds__(NTC) k_rates(const float* __restrict__ G, int64_t ld_g,
                                                const float* __restrict__ P, int64_t I, int J,
                                                float2 N0, float w_log2e, float* __restrict__ R,
-                                               int64_t ld_r, int vec_out) {
+                                               int64_t ld_r, int vec_out, float inv_mu, float* __restrict__ C,
+                                               int64_t ld_c, int vec_c, unsigned long long* bad) {
+    unsigned long long nbad = 0;
     constexpr int TT = 32 * TW, NTEAMS = NTC / TT;
     __shared__ float2 red[2 * NTEAMS * TW];
     const Team<TW> tm;
@@ -79,7 +83,6 @@ __global__ void __launch_bounds__(NTC) k_rates(const float* __restrict__ G, int6
         T = df_add2(T, N0);
         const float T_hi = T.x;
         const float T_lo = T.y;
-        float* rrow = R + i * ld_r;
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             const int col = 4 * (tm.tl + TT * v);
@@ -91,28 +94,53 @@ __global__ void __launch_bounds__(NTC) k_rates(const float* __restrict__ G, int6
                 const float sinr = interf > 0.f ? own / interf : INFINITY;
                 comp(r, c) = w_log2e * log1pf(sinr);
             }
-            if (col + 4 <= J && vec_out) {
-                *reinterpret_cast<float4*>(rrow + col) = r;
-            } else {
+            if (R) {
+                float* rrow = R + i * ld_r;
+                if (col + 4 <= J && vec_out) {
+                    *reinterpret_cast<float4*>(rrow + col) = r;
+                } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (col + c < J) rrow[col + c] = comp(r, c);
+                    for (int c = 0; c < 4; ++c)
+                        if (col + c < J) rrow[col + c] = comp(r, c);
+                }
+            }
+            if (C) {
+                float4 o;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float rv = comp(r, c);
+                    nbad += (col + c < J) && !(rv > 0.0f && isfinite(rv));
+                    comp(o, c) = __fdiv_rn(inv_mu, rv);
+                }
+                float* crow = C + i * ld_c;
+                if (col + 4 <= J && vec_c) {
+                    *reinterpret_cast<float4*>(crow + col) = o;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (col + c < J) crow[col + c] = comp(o, c);
+                }
             }
         }
     }
+    if (nbad) atomicAdd(bad, nbad);
 }
 
 ot_status launch_rates(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const float* P, int64_t I, int J,
-                       double N0, double W, float* R, int64_t ld_r, cudaStream_t s) {
+                       double N0, double W, float* R, int64_t ld_r, cudaStream_t s, double mu, float* C,
+                       int64_t ld_c, unsigned long long* bad_dev) {
     if (ld_g % 4 != 0 || ((uintptr_t)G & 15u))
         return set_error(ctx, OT_EINVAL, "G rows must be 16-byte aligned (ld_g %% 4 == 0, aligned base)");
-    const int vec_out = (ld_r % 4 == 0) && !((uintptr_t)R & 15u);
+    const int vec_out = R && (ld_r % 4 == 0) && !((uintptr_t)R & 15u);
+    const int vec_c = C && (ld_c % 4 == 0) && !((uintptr_t)C & 15u);
+    const float inv_mu = C ? (float)(1.0 / mu) : 0.0f;
     const float w_log2e = (float)(W / 0.69314718055994530942);
     const int nteams = NTC / (32 * (J <= 1024 ? 1 : (J <= 2048 ? 2 : (J <= 4096 ? 4 : 8))));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((I + nteams - 1) / nteams, 8LL * ctx->num_sms));
     const float n0_hi = (float)N0;
     const float2 n0 = make_float2(n0_hi, (float)(N0 - (double)n0_hi));
-    OTA_ROW_DISPATCH(J, k_rates, <<<grid, NTC, 0, s>>>(G, ld_g, P, I, J, n0, w_log2e, R, ld_r, vec_out));
+    OTA_ROW_DISPATCH(J, k_rates, <<<grid, NTC, 0, s>>>(G, ld_g, P, I, J, n0, w_log2e, R, ld_r, vec_out, inv_mu, C,
+                                                       ld_c, vec_c, bad_dev));
     ctx->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "rates launch");

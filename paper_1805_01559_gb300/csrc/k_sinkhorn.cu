@@ -71,6 +71,33 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve(SolveParams P, Strea
     sk_consumers<TW, VPT>(P, S, g, &sh, dyn, r0, r1, &par);
 }
 
+// Euclidean cost formed on the fly (Sec. IV cost choice (i)): no matrix is read, so there is
+// no producer; the RRH coordinates are staged once in the ring's space and every sweep forms
+// C_ij = ||x_i - x_j|| from them and the device's coordinates.
+template <int TW, int VPT>
+__global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve_euclid(SolveParams P, StreamCfg S) {
+    constexpr int NCW = Cons<TW>::NCW;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ SkShared sh;
+    float* rx = reinterpret_cast<float*>(dyn + S.off_ring);
+    for (int j = threadIdx.x; j < P.Jp; j += blockDim.x) {
+        const float2 r = j < P.J ? P.rrh_xy[j] : make_float2(0.f, 0.f);
+        rx[j] = r.x;
+        rx[P.Jp + j] = r.y;
+    }
+    if (threadIdx.x == 0) {
+        sh.s_stop = 0;
+        sh.s_bad = 0;
+    }
+    __syncthreads();
+    if ((int)(threadIdx.x >> 5) == NCW) return;  // no rows to stream
+    int64_t r0, r1;
+    cta_rows(P.I, S.rows_per_stage, P.V, blockIdx.x, gridDim.x, &r0, &r1);
+    GroupCtx g{(int)gridDim.x, (int)blockIdx.x, &P.st->bar, 0u, &P.st->status, &P.st->status};
+    int par = 0;
+    sk_consumers<TW, VPT, true>(P, S, g, &sh, dyn, r0, r1, &par);
+}
+
 // Several solves sharing one cost matrix (sk_multi.cuh): the same launch structure.
 template <int TW, int VPT, int NS, bool RC>
 __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve_multi(MultiParams M, StreamCfg S) {
@@ -196,28 +223,31 @@ struct Kernels {
     int tw, vpt, ncw;
 };
 
-template <int TW, int VPT>
+template <int TW, int VPT, bool EUC>
 Kernels kernels_for() {
-    return Kernels{(const void*)sk_solve<TW, VPT>, TW, VPT, Cons<TW>::NCW};
+    if constexpr (EUC) return Kernels{(const void*)sk_solve_euclid<TW, VPT>, TW, VPT, Cons<TW>::NCW};
+    else return Kernels{(const void*)sk_solve<TW, VPT>, TW, VPT, Cons<TW>::NCW};
 }
 
 // One-warp teams (TW = 1) get VPT = ceil(J4 / 32) exactly; chunk_inside() relies on it.
-bool pick_kernels(int J, Kernels* k) {
+template <bool EUC>
+bool pick_kernels_t(int J, Kernels* k) {
     const int J4 = (J + 3) / 4;
-    if (J4 <= 32) *k = kernels_for<1, 1>();
-    else if (J4 <= 64) *k = kernels_for<1, 2>();
-    else if (J4 <= 96) *k = kernels_for<1, 3>();
-    else if (J4 <= 128) *k = kernels_for<1, 4>();
-    else if (J4 <= 160) *k = kernels_for<1, 5>();
-    else if (J4 <= 192) *k = kernels_for<1, 6>();
-    else if (J4 <= 224) *k = kernels_for<1, 7>();
-    else if (J4 <= 256) *k = kernels_for<1, 8>();
-    else if (J4 <= 512) *k = kernels_for<2, 8>();
-    else if (J4 <= 1024) *k = kernels_for<4, 8>();
-    else if (J4 <= 2048) *k = kernels_for<8, 8>();
+    if (J4 <= 32) *k = kernels_for<1, 1, EUC>();
+    else if (J4 <= 64) *k = kernels_for<1, 2, EUC>();
+    else if (J4 <= 96) *k = kernels_for<1, 3, EUC>();
+    else if (J4 <= 128) *k = kernels_for<1, 4, EUC>();
+    else if (J4 <= 160) *k = kernels_for<1, 5, EUC>();
+    else if (J4 <= 192) *k = kernels_for<1, 6, EUC>();
+    else if (J4 <= 224) *k = kernels_for<1, 7, EUC>();
+    else if (J4 <= 256) *k = kernels_for<1, 8, EUC>();
+    else if (J4 <= 512) *k = kernels_for<2, 8, EUC>();
+    else if (J4 <= 1024) *k = kernels_for<4, 8, EUC>();
+    else if (J4 <= 2048) *k = kernels_for<8, 8, EUC>();
     else return false;
     return true;
 }
+bool pick_kernels(int J, Kernels* k) { return pick_kernels_t<false>(J, k); }
 
 // Stage geometry, shared-memory layout and grid of the persistent kernel: one CTA per row
 // partition (at most one per SM).
@@ -374,6 +404,8 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
     P.eps_ln2 = a.eps * LN2;
     P.F_in = mode.F_in;
     P.G_in = mode.G_in;
+    P.dev_xy = a.dev_xy;
+    P.rrh_xy = a.rrh_xy;
     if (ctx) timing_mark(ctx, 1, s);
     if (kev0) cudaEventRecord(kev0, s);
     {
@@ -423,7 +455,9 @@ ot_status enqueue_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary*
     const int64_t I = a.I;
     const int Jp = (int)round_up(J, 4);
     Kernels kk;
-    if (!pick_kernels(J, &kk)) return set_error(ctx, OT_EUNSUPPORTED, "J=%d above 8192", J);
+    const bool euc = a.dev_xy != nullptr;
+    if (!(euc ? pick_kernels_t<true>(J, &kk) : pick_kernels(J, &kk)))
+        return set_error(ctx, OT_EUNSUPPORTED, "J=%d above 8192", J);
     LoopLaunch LL;
     st = plan_solve(kk, I, Jp, a.ld, ctx->num_sms, 1 << 30, &LL);
     if (st) return set_error(ctx, st, "solver does not fit the shared memory (I=%lld J=%d)", (long long)I, J);

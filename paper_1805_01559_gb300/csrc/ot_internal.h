@@ -111,6 +111,8 @@ struct SolveArgs {
     ot_assoc_result* out;
     cudaStream_t stream;
     const unsigned long long* input_bad = nullptr;  // nonzero count => invalid input (checked on device)
+    const float2* dev_xy = nullptr;  // Euclidean cost on the fly: device and RRH coordinates (C unused)
+    const float2* rrh_xy = nullptr;
 };
 
 // FP32 log-domain solve (Algorithm 1).  Fills `sum_host` (synchronises).
@@ -146,8 +148,11 @@ ot_status f32_first_iteration(ot_assoc_ctx* ctx, const SolveArgs& a, float2* F_o
 ot_status f32_finalize_on(ot_assoc_ctx* ctx, const SolveArgs& a, const float2* F_in, const double* G_in, int iters,
                           double err, int converged, SolveSummary* sum_host);
 
+// Rates into R (may be null when C is given); with C non-null also C = (1/mu)/R in the same
+// pass, counting rates that are not finite and > 0 into *bad_dev.
 ot_status launch_rates(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const float* P, int64_t I,
-                       int J, double N0, double W, float* R, int64_t ld_r, cudaStream_t s);
+                       int J, double N0, double W, float* R, int64_t ld_r, cudaStream_t s, double mu = 1.0,
+                       float* C = nullptr, int64_t ld_c = 0, unsigned long long* bad_dev = nullptr);
 // C = 1/(mu R); pads columns [J, ld_c) with +inf when pad_inf; counts invalid R into *bad_dev.
 ot_status launch_cost(ot_assoc_ctx* ctx, const float* R, int64_t ld_r, int64_t I, int J, double mu,
                       float* C, int64_t ld_c, bool pad_inf, unsigned long long* bad_dev,

@@ -150,6 +150,30 @@ __device__ __forceinline__ void load_row_smem(const float* row, int J, int tl, f
     }
 }
 
+// Euclidean cost of four columns from coordinates: sqrt(dx^2 + dy^2) in FP32 with explicit
+// roundings (no contraction), so any IEEE single-precision evaluation of the same formula
+// gives the same values; columns at or past J give +inf (no mass).
+__device__ __forceinline__ float4 euclid_chunk(float2 d, const float* rx, const float* ry, int col, int J) {
+    float4 a = *reinterpret_cast<const float4*>(rx + col);
+    float4 b = *reinterpret_cast<const float4*>(ry + col);
+    float4 o;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float dx = __fsub_rn(d.x, comp(a, c));
+        const float dy = __fsub_rn(d.y, comp(b, c));
+        comp(o, c) = col + c < J ? __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy))) : INFINITY;
+    }
+    return o;
+}
+template <int TW, int VPT>
+__device__ __forceinline__ void euclid_row(float2 d, const float* rx, const float* ry, int J, int tl, float4 (&x)[VPT]) {
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int col = 4 * (tl + 32 * TW * v);
+        x[v] = col < J ? euclid_chunk(d, rx, ry, col, J) : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+    }
+}
+
 // Producer: stream the CTA's row blocks sweep after sweep until the consumers raise s_stop,
 // then wait for every copy still in flight before leaving.
 template <typename T>
@@ -235,6 +259,11 @@ struct SolveParams {
     // potentials F' (pairs) and G (log2 units).
     const float2* F_in;  // [I]
     const double* G_in;  // [Jp]
+    // Euclidean cost formed on the fly (Sec. IV cost choice (i)) instead of read from C:
+    // device and RRH coordinates; the RRH coordinates are staged in shared memory at the
+    // ring's offset (x then y, Jp floats each).
+    const float2* dev_xy;  // [I]
+    const float2* rrh_xy;  // [J]
 };
 
 // Row partitions.  The I rows form B = ceil(I / rs) stage blocks of rs rows; partition v of V
@@ -416,7 +445,7 @@ __device__ __forceinline__ void cta_col_sum(float* comb, const float4 (&acc)[VPT
 // sums (in team order) into the partition's FP64 partials P.fpart[v]; the row residual
 // sum_i p^_i |sum_j t_ij - 1| uses error-free row sums.
 static constexpr int FIN_ROWS = 16;
-template <int TW, int VPT>
+template <int TW, int VPT, bool EUC = false>
 __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const StreamCfg& S, SkShared* sh,
                                                   unsigned char* dyn, int64_t r0, int nrow, int v0, int v1,
                                                   const float2* Fold, uint32_t& cseq, int* abort) {
@@ -428,6 +457,7 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
     const float* Gs = reinterpret_cast<const float*>(dyn + S.off_G);
     const float* Ps = reinterpret_cast<const float*>(dyn + S.off_P);
     const float* ring = reinterpret_cast<const float*>(dyn + S.off_ring);
+    const float* rx = ring;  // Euclidean cost: RRH x then y coordinates
     const int tid = threadIdx.x, lane = tid & 31;
     const int J = P.J, Jp = P.Jp, rs_ = S.rows_per_stage;
     const Team<TW> tm;
@@ -447,7 +477,7 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
     for (int kb = 0; kb < nblk; ++kb) {
         const int st = (int)(cseq % (uint32_t)S.stages);
         const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
-        const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, abort);
+        const bool ok = EUC || mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, abort);
         const int lr0 = kb * rs_;
         const int rows = min(rs_, nrow - lr0);
         const float* stage = ring + (size_t)st * S.stage_floats;
@@ -456,6 +486,7 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
             if (rr >= rows) break;
             const int lr = lr0 + rr;
             const float* row = stage + (size_t)rr * P.ld;
+            const float2 dxy = EUC ? __ldg(P.dev_xy + r0 + lr) : make_float2(0.f, 0.f);
             const float2 F = Fold[lr];
             const float phat = Ps[lr];
             const int64_t i = r0 + lr;
@@ -465,7 +496,7 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
             for (int v = 0; v < VPT; ++v) {
                 const int col = 4 * (tm.tl + TT * v);
                 if (chunk_inside<TW, VPT>(v) || col < J) {
-                    float4 x = *reinterpret_cast<const float4*>(row + col);
+                    float4 x = EUC ? euclid_chunk(dxy, rx, rx + Jp, col, J) : *reinterpret_cast<const float4*>(row + col);
                     float4 gv = *reinterpret_cast<const float4*>(Gs + col);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
@@ -487,7 +518,7 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
             errt = fmaf(phat, fabsf((r.x - 1.0f) + r.y), errt);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[st]);
+        if (!EUC && lane == 0) mbar_arrive(&empty[st]);
         ++cseq;
         const bool at_end = (kb + 1 == vend);
         if ((kb + 1 - vbeg) % every == 0 || at_end) {
@@ -526,7 +557,7 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
 // potential buffer *ret_par of shared memory, and in P.F_out when given), false when the
 // instance failed or a wait gave up.  Either way s_stop is raised for the producer.
 // Every decision that ends the loop is taken identically by every CTA of the group.
-template <int TW, int VPT>
+template <int TW, int VPT, bool EUC = false>
 __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamCfg& S, GroupCtx& g, SkShared* sh,
                                              unsigned char* dyn, int64_t r0, int64_t r1, int* ret_par) {
     constexpr int NCW = Cons<TW>::NCW;
@@ -540,6 +571,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
     float2* Fs = reinterpret_cast<float2*>(dyn + S.off_F);     // [2][rmax]
     float* Ps = reinterpret_cast<float*>(dyn + S.off_P);       // [rmax]
     float* ring = reinterpret_cast<float*>(dyn + S.off_ring);  // [stages][stage_floats]
+    const float* rxs = ring;  // Euclidean cost: RRH x then y coordinates [2][Jp]
     float* red = sh->red;
     float* errf = sh->errf;
     double(*sh_sum)[2] = sh->sh_sum;
@@ -666,7 +698,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
         load_G_smem(P.G_in, J, Jp, Gs, tid, NC);
         bar_named(CONS_BAR, NC);
         *ret_par = 0;
-        sk_finalize_sweep<TW, VPT>(P, S, sh, dyn, r0, nrow, v0, v1, Fs, cseq, g.abort);
+        sk_finalize_sweep<TW, VPT, EUC>(P, S, sh, dyn, r0, nrow, v0, v1, Fs, cseq, g.abort);
         if (tid == 0) s_stop = 1;
         return true;
     }
@@ -690,7 +722,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
           for (; kb < vend; ++kb) {
             const int st = (int)(cseq % (uint32_t)S.stages);
             const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
-            const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, g.abort);
+            const bool ok = EUC || mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, g.abort);
             const int lr0 = kb * rs_;
             const int rows = min(rs_, nrow - lr0);
             const float* stage = ring + (size_t)st * S.stage_floats;
@@ -698,7 +730,10 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                 const int rr = tm.team + NTEAMS * j;
                 if (rr >= rows) break;
                 float4 x[VPT];
-                load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
+                if constexpr (EUC)
+                    euclid_row<TW, VPT>(__ldg(P.dev_xy + r0 + lr0 + rr), rxs, rxs + Jp, J, tm.tl, x);
+                else
+                    load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
                 // row maximum of y = G0 - k C (approximate values suffice for the shift)
                 float m = -INFINITY;
 #pragma unroll
@@ -746,7 +781,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                     }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[st]);
+            if (!EUC && lane == 0) mbar_arrive(&empty[st]);
             ++cseq;
           }
             // end of partition vp: merge the teams' (max, sum) pairs in two rounds through
@@ -869,7 +904,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
           for (; kb < vend; ++kb) {
             const int st = (int)(cseq % (uint32_t)S.stages);
             const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
-            const bool ok = mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, g.abort);
+            const bool ok = EUC || mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, g.abort);
             const int lr0 = kb * rs_;
             const int rows = min(rs_, nrow - lr0);
             const float* stage = ring + (size_t)st * S.stage_floats;
@@ -878,7 +913,10 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                 if (rr >= rows) break;
                 const int lr = lr0 + rr;
                 float4 x[VPT];
-                load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
+                if constexpr (EUC)
+                    euclid_row<TW, VPT>(__ldg(P.dev_xy + r0 + lr), rxs, rxs + Jp, J, tm.tl, x);
+                else
+                    load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
                 const float2 F = Fold[lr];
                 float rsum = 0.f;
 #pragma unroll
@@ -912,7 +950,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[st]);
+            if (!EUC && lane == 0) mbar_arrive(&empty[st]);
             ++cseq;
           }
             // end of partition vp: its column partials (teams in order) and row residual
@@ -972,7 +1010,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             if (P.F_out)
                 for (int r = tid; r < nrow; r += NC) P.F_out[r0 + r] = Fold[r];
             *ret_par = (s - 1) & 1;
-            if (P.fpart) sk_finalize_sweep<TW, VPT>(P, S, sh, dyn, r0, nrow, v0, v1, Fold, cseq, g.abort);
+            if (P.fpart) sk_finalize_sweep<TW, VPT, EUC>(P, S, sh, dyn, r0, nrow, v0, v1, Fold, cseq, g.abort);
             if (tid == 0) s_stop = 1;
             return true;
         }

@@ -326,3 +326,24 @@ def test_bounded_barrier_reports_timeout(ctx):
         ctx.set_spin_limit(0)
     res = ctx.solve_cost(_t(C), _t(p), _t(q), 0.05, tol=1e-6, max_iter=2000)
     assert res.status == binding.OT_OK
+
+
+
+def test_cost_from_gains_equals_rates_then_cost(ctx):
+    """Rates and cost in one pass give the same values as the two calls."""
+    from paper_1805_01559_gb300 import instances
+    inst = instances.config1()
+    G = torch.from_numpy(inst.G.astype(np.float32)).cuda()
+    P = torch.from_numpy(inst.P.astype(np.float32)).cuda()
+    R = ctx.build_rates(G, P, inst.N0, inst.W_hz)
+    C_ref, eps_ref = ctx.build_cost(R, inst.mu, eps_rel=0.05)
+    R2 = torch.empty_like(R)
+    C, eps = ctx.build_cost_from_gains(G, P, inst.N0, inst.W_hz, inst.mu, eps_rel=0.05, R_out=R2)
+    assert torch.equal(R2, R) and torch.equal(C, C_ref) and eps == eps_ref
+    C3, none = ctx.build_cost_from_gains(G, P, inst.N0, inst.W_hz, inst.mu)
+    assert none is None and torch.equal(C3, C_ref)
+    G0 = G.clone()
+    G0[5, :] = 0.0  # a device that hears nothing: zero rates
+    from paper_1805_01559_gb300 import binding
+    with pytest.raises(binding.OTError):
+        ctx.build_cost_from_gains(G0, P, inst.N0, inst.W_hz, inst.mu, eps_rel=0.05)
