@@ -34,22 +34,19 @@ static constexpr int NTC = 256;
 // With C non-null the same pass also writes the cost C_ij = (1/mu) / R_ij (one IEEE FP32
 // division, as k_cost) and counts rates that are not finite and > 0; R may then be null.
 template <int TW, int VPT>
-__global__ void __launch_bounds__(NTC) k_rates(const float* __restrict__ G, int64_t ld_g,
+__global__ void __launch_bounds__(NTC, 3) k_rates(const float* __restrict__ G, int64_t ld_g,
                                                const float* __restrict__ P, int64_t I, int J,
                                                float2 N0, float w_log2e, float* __restrict__ R,
                                                int64_t ld_r, int vec_out, float inv_mu, float* __restrict__ C,
                                                int64_t ld_c, int vec_c, unsigned long long* bad) {
     unsigned long long nbad = 0;
     constexpr int TT = 32 * TW, NTEAMS = NTC / TT;
+    constexpr int JMAX = 4 * TT * VPT;  // columns a team covers
     __shared__ float2 red[2 * NTEAMS * TW];
+    __shared__ __align__(16) float pws[JMAX];  // transmit powers (0 past J): shared, not per-thread registers
     const Team<TW> tm;
-    float4 pw[VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-        const int col = 4 * (tm.tl + TT * v);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) comp(pw[v], c) = (col + c < J) ? P[col + c] : 0.0f;
-    }
+    for (int j = threadIdx.x; j < JMAX; j += NTC) pws[j] = j < J ? P[j] : 0.0f;
+    __syncthreads();
     int par = 0;
     const int64_t team_g = (int64_t)blockIdx.x * NTEAMS + tm.team;
     const int64_t nteams_g = (int64_t)gridDim.x * NTEAMS;
@@ -57,19 +54,19 @@ __global__ void __launch_bounds__(NTC) k_rates(const float* __restrict__ G, int6
         float4 x[VPT];
         load_row<TW, VPT>(G + i * ld_g, J, tm.tl, x, 0.0f);
         float s = 0.f, cmp = 0.f;
-        float4 lo[VPT];
 #pragma unroll
-        for (int v = 0; v < VPT; ++v)
+        for (int v = 0; v < VPT; ++v) {
+            float4 pw = *reinterpret_cast<const float4*>(pws + 4 * (tm.tl + TT * v));
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const float hi = comp(pw[v], c) * comp(x[v], c);
-                comp(lo[v], c) = fmaf(comp(pw[v], c), comp(x[v], c), -hi);
-                comp(x[v], c) = hi;
+                const float hi = comp(pw, c) * comp(x[v], c);
+                const float lo = fmaf(comp(pw, c), comp(x[v], c), -hi);
                 const float t = s + hi;
                 cmp += (fabsf(s) >= fabsf(hi)) ? ((s - t) + hi) : ((hi - t) + s);
-                cmp += comp(lo[v], c);
+                cmp += lo;
                 s = t;
             }
+        }
         // row total as an FP32 pair: warp sum of the (sum, compensation) pairs, then the team
         float2 T = warp_sum_df(make_float2(s, cmp));
         if constexpr (TW > 1) {
@@ -86,11 +83,14 @@ __global__ void __launch_bounds__(NTC) k_rates(const float* __restrict__ G, int6
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             const int col = 4 * (tm.tl + TT * v);
+            float4 pw = *reinterpret_cast<const float4*>(pws + col);
             float4 r;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const float own = comp(x[v], c);
-                const float interf = (T_hi - own) + (T_lo - comp(lo[v], c));
+                // the own term as the same exact pair as in the row total
+                const float own = comp(pw, c) * comp(x[v], c);
+                const float own_lo = fmaf(comp(pw, c), comp(x[v], c), -own);
+                const float interf = (T_hi - own) + (T_lo - own_lo);
                 const float sinr = interf > 0.f ? own / interf : INFINITY;
                 comp(r, c) = w_log2e * log1pf(sinr);
             }
