@@ -244,7 +244,7 @@ def run_gpu(args):
     gs = [torch.empty(J, dtype=torch.float64, device=dev) for _ in EPS_REL]
     ctx = binding.Context(local)
     ctx.enable_timing(True)
-    loop_ms, loop_bytes, loop_launches = [], [], 0
+    loop_ms, loop_bytes = [], []
     iters_seen = []
 
     def step(record=False):
@@ -601,7 +601,7 @@ def run_c5(args):
     ctx = binding.Context(0)
     srv = ctx.server(group_ctas=args.c5_group)
     t0 = time.perf_counter()
-    ids, resident = [], 0
+    ids = []
     gen = list(pool.imap(_gen_c5, shapes, chunksize=1))
     pool.close()
     try:
@@ -742,7 +742,7 @@ def run_alg2(args):
                                    f"delta = 5% of an equal share", "I": I, "J": J, "outer": outer, "tol": TOL,
                        "l2": "C (160 MB) larger than L2"},
             "outer_steps_per_s": outer / (ms / 1e3),
-            "host_loop": {"ms": statistics.median(ms_h), "iters": its_h,
+            "host_loop": {"ms": statistics.median(ms_h), "iters": its_h, "max_load_last": ml_h[-1],
                           "fused_speedup": statistics.median(ms_h) / ms},
             "iters": iters, "max_load": {"first": ml[0], "last": ml[-1], "min": min(ml)},
             "jstar": [st["jstar"] for st in res.steps],

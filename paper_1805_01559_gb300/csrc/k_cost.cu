@@ -34,7 +34,7 @@ static constexpr int NTC = 256;
 // With C non-null the same pass also writes the cost C_ij = (1/mu) / R_ij (one IEEE FP32
 // division, as k_cost) and counts rates that are not finite and > 0; R may then be null.
 template <int TW, int VPT>
-__global__ void __launch_bounds__(NTC, 3) k_rates(const float* __restrict__ G, int64_t ld_g,
+__global__ void __launch_bounds__(NTC, 2) k_rates(const float* __restrict__ G, int64_t ld_g,
                                                const float* __restrict__ P, int64_t I, int J,
                                                float2 N0, float w_log2e, float* __restrict__ R,
                                                int64_t ld_r, int vec_out, float inv_mu, float* __restrict__ C,
