@@ -159,7 +159,10 @@ __global__ void __launch_bounds__(256) lp_build(const float* __restrict__ C, int
 
 // Consumer warps of the stored-kernel loop.  Returns false when the launch must end early
 // (failed instance or a wait that gave up).
-template <typename T, int TW, int VPT>
+// RR: a row's values are read twice from the staged stage (once for the row sum, once for the
+// column partials) instead of being kept in registers, so a lane can hold twice the columns'
+// accumulators and rows of 4096 columns keep narrow teams (more rows in flight per CTA).
+template <typename T, int TW, int VPT, bool RR>
 __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg& S, GroupCtx& g, SkShared* sh,
                                              unsigned char* dyn, int64_t r0, int64_t r1) {
     constexpr int N = Chunk<T>::N;
@@ -280,25 +283,29 @@ __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg&
                     if (rr >= rows) break;
                     const int lr = lr0 + rr;
                     const T* row = stage + (size_t)rr * P.ldk;
-                    float x[VPT][N];
+                    float x[RR ? 1 : VPT][N];
                     float ssum = 0.f;
 #pragma unroll
                     for (int v = 0; v < VPT; ++v) {
                         const int col = N * (tm.tl + TT * v);
+                        float xv[N];
                         if (col < J) {
-                            Chunk<T>::load(row + col, x[v]);
+                            Chunk<T>::load(row + col, xv);
 #pragma unroll
                             for (int e = 0; e < N; e += 4) {  // beta four at a time (16-byte loads)
                                 const float4 bq = *reinterpret_cast<const float4*>(Bs + col + e);
-                                ssum = fmaf(x[v][e], bq.x, ssum);
-                                ssum = fmaf(x[v][e + 1], bq.y, ssum);
-                                ssum = fmaf(x[v][e + 2], bq.z, ssum);
-                                ssum = fmaf(x[v][e + 3], bq.w, ssum);
+                                ssum = fmaf(xv[e], bq.x, ssum);
+                                ssum = fmaf(xv[e + 1], bq.y, ssum);
+                                ssum = fmaf(xv[e + 2], bq.z, ssum);
+                                ssum = fmaf(xv[e + 3], bq.w, ssum);
                             }
                         } else {
 #pragma unroll
-                            for (int e = 0; e < N; ++e) x[v][e] = 0.f;
+                            for (int e = 0; e < N; ++e) xv[e] = 0.f;
                         }
+                        if constexpr (!RR)
+#pragma unroll
+                            for (int e = 0; e < N; ++e) x[v][e] = xv[e];
                     }
                     ssum = team_reduce<TW, float, false>(ssum, sh->red, NTEAMS, tm, par);
                     const float ph = Ps[lr];
@@ -308,10 +315,23 @@ __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg&
                     absorb |= fabsf(__log2f(an)) > tau;
                     if (tm.tl == 0) Anew[lr] = an;
                     const float w = ph * an;
+                    if constexpr (RR) {
 #pragma unroll
-                    for (int v = 0; v < VPT; ++v)
+                        for (int v = 0; v < VPT; ++v) {
+                            const int col = N * (tm.tl + TT * v);
+                            if (col < J) {
+                                float xv[N];
+                                Chunk<T>::load(row + col, xv);
 #pragma unroll
-                        for (int e = 0; e < N; ++e) acc[v][e] = fmaf(x[v][e], w, acc[v][e]);
+                                for (int e = 0; e < N; ++e) acc[v][e] = fmaf(xv[e], w, acc[v][e]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < VPT; ++v)
+#pragma unroll
+                            for (int e = 0; e < N; ++e) acc[v][e] = fmaf(x[v][e], w, acc[v][e]);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[st]);
@@ -443,7 +463,7 @@ __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg&
 #undef LP_BARRIER
 }
 
-template <typename T, int TW, int VPT>
+template <typename T, int TW, int VPT, bool RR>
 __global__ void __launch_bounds__(Cons<TW>::NT, 1) lp_loop(LpParams P, StreamCfg S) {
     constexpr int NCW = Cons<TW>::NCW;
     extern __shared__ __align__(128) unsigned char dyn[];
@@ -471,7 +491,7 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) lp_loop(LpParams P, StreamCfg
         return;
     }
     GroupCtx g{(int)gridDim.x, (int)blockIdx.x, &P.st->bar, 0u, &P.st->status, &P.st->status};
-    lp_consumers<T, TW, VPT>(P, S, g, &sh, dyn, r0, r1);
+    lp_consumers<T, TW, VPT, RR>(P, S, g, &sh, dyn, r0, r1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -482,13 +502,14 @@ struct LpKernel {
     int tw, ncw;
 };
 
-template <typename T, int TW, int VPT>
+template <typename T, int TW, int VPT, bool RR = false>
 LpKernel lp_kernel() {
-    return LpKernel{(const void*)lp_loop<T, TW, VPT>, TW, Cons<TW>::NCW};
+    return LpKernel{(const void*)lp_loop<T, TW, VPT, RR>, TW, Cons<TW>::NCW};
 }
 
-// One-warp teams while a lane holds at most 32 values (8 chunks of 4 or 4 of 8), wider teams
-// beyond.
+// One-warp teams while a lane holds at most 32 values (8 chunks of 4 or 4 of 8); 16-bit
+// kernels then read each row twice from shared memory to hold 64 accumulators a lane (8
+// chunks of 8); wider teams beyond.
 template <typename T>
 bool lp_pick(int J, LpKernel* k) {
     constexpr int N = Chunk<T>::N;
@@ -506,9 +527,9 @@ bool lp_pick(int J, LpKernel* k) {
         if (Jc <= 32) *k = lp_kernel<T, 1, 1>();
         else if (Jc <= 64) *k = lp_kernel<T, 1, 2>();
         else if (Jc <= 128) *k = lp_kernel<T, 1, 4>();
-        else if (Jc <= 256) *k = lp_kernel<T, 2, 4>();
-        else if (Jc <= 512) *k = lp_kernel<T, 4, 4>();
-        else if (Jc <= 1024) *k = lp_kernel<T, 8, 4>();
+        else if (Jc <= 256) *k = lp_kernel<T, 1, 8, true>();
+        else if (Jc <= 512) *k = lp_kernel<T, 2, 8, true>();
+        else if (Jc <= 1024) *k = lp_kernel<T, 4, 8, true>();
         else return false;
     }
     return true;
@@ -562,6 +583,25 @@ ot_status lowp_solve_t(ot_assoc_ctx* ctx, const SolveArgs& a, double absorb_log2
     LpState* lst = (LpState*)(base + o_st);
     LpState* hls = (LpState*)host_staging(ctx, sizeof(LpState) + sizeof(SolveSummary), &st);
     if (st) return st;
+    // phase events (timing mode only): [0] before iteration 1, then a pair around each loop
+    // launch, and the last one after the finalize
+    const bool timing = ctx->timing;
+    cudaEvent_t tev[2 + 2 * 8] = {};
+    int ntev = 0;
+    auto mark = [&](void) {
+        if (!timing || ntev >= (int)(sizeof(tev) / sizeof(tev[0]))) return;
+        if (cudaEventCreate(&tev[ntev]) == cudaSuccess) cudaEventRecord(tev[ntev++], s);
+        else cudaGetLastError();
+    };
+    struct EvGuard {
+        cudaEvent_t* e;
+        int* n;
+        ~EvGuard() {
+            for (int i = 0; i < *n; ++i) cudaEventDestroy(e[i]);
+        }
+    } evguard{tev, &ntev};
+    int loop_reads = 0;
+    mark();
     // iteration 1 in the log domain from C
     int dstat = 0;
     st = f32_first_iteration(ctx, a, Fm, Gm, &dstat);
@@ -609,8 +649,10 @@ ot_status lowp_solve_t(ot_assoc_ctx* ctx, const SolveArgs& a, double absorb_log2
         P.tau = (float)tau;
         P.spin = ctx->spin_limit;
         void* args[] = {&P, &S};
+        mark();
         e = cudaLaunchCooperativeKernel(kk.fn, dim3(grid), dim3(32 * (kk.ncw + 1)), args, smem, s);
         if (e != cudaSuccess) return cuda_error(ctx, e, "stored-kernel loop launch");
+        mark();
         ctx->launches += 2;
         e = cudaMemcpyAsync(hls, lst, sizeof(LpState), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -621,6 +663,7 @@ ot_status lowp_solve_t(ot_assoc_ctx* ctx, const SolveArgs& a, double absorb_log2
             sum_host->iters = hls->iters;
             return OT_OK;
         }
+        loop_reads += hls->iters + 1 - iters;  // the launch read K~ once per iteration and once to test
         iters = hls->iters;
         err = hls->err;
         converged = hls->converged;
@@ -630,6 +673,25 @@ ot_status lowp_solve_t(ot_assoc_ctx* ctx, const SolveArgs& a, double absorb_log2
     st = f32_finalize_on(ctx, a, Fm, Gm, iters, err, converged, sum_host);
     if (st) return st;
     sum_host->absorptions = absorptions;
+    mark();
+    if (timing && ntev >= 4 && cudaEventSynchronize(tev[ntev - 1]) == cudaSuccess) {
+        // init: iteration 1 and the first kernel build; loop: the persistent loop launches;
+        // finalize: everything after the last loop launch (rebuilds between launches count as loop)
+        float a0 = 0.f, lp = 0.f, fin = 0.f, x = 0.f;
+        cudaEventElapsedTime(&a0, tev[0], tev[1]);
+        for (int i = 1; i + 1 < ntev - 1; i += 2) {
+            if (cudaEventElapsedTime(&x, tev[i], tev[i + 1]) == cudaSuccess) lp += x;
+        }
+        cudaEventElapsedTime(&fin, tev[ntev - 2], tev[ntev - 1]);
+        ot_assoc_timings t = {};
+        t.init_ms = a0;
+        t.loop_ms = lp;
+        t.finalize_ms = fin;
+        t.sweeps = loop_reads;
+        t.valid = 1;
+        ctx->last_timings = t;
+    }
+    cudaGetLastError();
     return OT_OK;
 }
 
