@@ -71,7 +71,8 @@ const char* ot_assoc_status_string(int status);
  */
 ot_status ot_assoc_create(ot_assoc_ctx** ctx, int device, size_t hbm_budget_bytes);
 
-/* Release the context and its scratch.  NULL is ignored. */
+/* Release the context and its scratch (first waiting for asynchronous solves still in
+ * flight).  NULL is ignored. */
 void ot_assoc_destroy(ot_assoc_ctx* ctx);
 
 /* Last error message of this context ("" if none).  Valid until the next call. */

@@ -228,6 +228,9 @@ ot_status ot_assoc_create(ot_assoc_ctx** out, int device, size_t hbm_budget_byte
 void ot_assoc_destroy(ot_assoc_ctx* ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
+    // asynchronous solves still in flight use the scratch freed below: let them finish
+    for (int i = 0; i < ot_assoc_ctx::kAsyncSlots; ++i)
+        if (ctx->async_ticket[i] && ctx->async_ev[i][0]) cudaEventSynchronize(ctx->async_ev[i][0]);
     for (auto& b : ctx->slots)
         if (b.ptr) cudaFree(b.ptr);
     if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
