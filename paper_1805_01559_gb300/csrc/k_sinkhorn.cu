@@ -72,10 +72,11 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve(SolveParams P, Strea
 }
 
 // Euclidean cost formed on the fly (Sec. IV cost choice (i)): no matrix is read, so there is
-// no producer; the RRH coordinates are staged once in the ring's space and every sweep forms
+// no producer warp (the block is the consumer warps alone, which leaves each thread more
+// registers); the RRH coordinates are staged once in the ring's space and every sweep forms
 // C_ij = ||x_i - x_j|| from them and the device's coordinates.
 template <int TW, int VPT>
-__global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve_euclid(SolveParams P, StreamCfg S) {
+__global__ void __launch_bounds__(Cons<TW>::NCW * 32, 1) sk_solve_euclid(SolveParams P, StreamCfg S) {
     constexpr int NCW = Cons<TW>::NCW;
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ SkShared sh;
@@ -90,7 +91,6 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) sk_solve_euclid(SolveParams P
         sh.s_bad = 0;
     }
     __syncthreads();
-    if ((int)(threadIdx.x >> 5) == NCW) return;  // no rows to stream
     int64_t r0, r1;
     cta_rows(P.I, S.rows_per_stage, P.V, blockIdx.x, gridDim.x, &r0, &r1);
     GroupCtx g{(int)gridDim.x, (int)blockIdx.x, &P.st->bar, 0u, &P.st->status, &P.st->status};
@@ -221,12 +221,13 @@ namespace {
 struct Kernels {
     const void* solve;
     int tw, vpt, ncw;
+    int nthreads;  // block size: the consumer warps, plus the producer warp where C is streamed
 };
 
 template <int TW, int VPT, bool EUC>
 Kernels kernels_for() {
-    if constexpr (EUC) return Kernels{(const void*)sk_solve_euclid<TW, VPT>, TW, VPT, Cons<TW>::NCW};
-    else return Kernels{(const void*)sk_solve<TW, VPT>, TW, VPT, Cons<TW>::NCW};
+    if constexpr (EUC) return Kernels{(const void*)sk_solve_euclid<TW, VPT>, TW, VPT, Cons<TW>::NCW, Cons<TW>::NCW * 32};
+    else return Kernels{(const void*)sk_solve<TW, VPT>, TW, VPT, Cons<TW>::NCW, Cons<TW>::NT};
 }
 
 // One-warp teams (TW = 1) get VPT = ceil(J4 / 32) exactly; chunk_inside() relies on it.
@@ -320,7 +321,7 @@ ot_status plan_solve_uncached(const Kernels& kk, int64_t I, int Jp, int64_t ld, 
         return OT_ECUDA;
     }
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk.solve, 32 * (kk.ncw + 1), L->smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk.solve, kk.nthreads, L->smem) != cudaSuccess) {
         cudaGetLastError();
         return OT_ECUDA;
     }
@@ -410,7 +411,7 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
     if (kev0) cudaEventRecord(kev0, s);
     {
         void* args[] = {&P, (void*)&LL.cfg};
-        e = cudaLaunchCooperativeKernel(kk.solve, dim3(LL.grid), dim3(32 * (kk.ncw + 1)), args, LL.smem, s);
+        e = cudaLaunchCooperativeKernel(kk.solve, dim3(LL.grid), dim3(kk.nthreads), args, LL.smem, s);
         if (e != cudaSuccess) return e;
     }
     if (kev1) cudaEventRecord(kev1, s);
@@ -479,7 +480,7 @@ ot_status enqueue_solve_f32(ot_assoc_ctx* ctx, const SolveArgs& a, SolveSummary*
 // team of a single solve), three solves on wider teams (4 chunks a lane).
 template <int TW, int VPT, int NS, bool RC>
 Kernels multi_for() {
-    return Kernels{(const void*)sk_solve_multi<TW, VPT, NS, RC>, TW, VPT, Cons<TW>::NCW};
+    return Kernels{(const void*)sk_solve_multi<TW, VPT, NS, RC>, TW, VPT, Cons<TW>::NCW, Cons<TW>::NT};
 }
 bool pick_multi(int J, int n, Kernels* k) {
     const int J4 = (J + 3) / 4;
@@ -535,7 +536,7 @@ ot_status launch_solve_multi(ot_assoc_ctx* ctx, const SolveArgs& a, int n, const
         return set_error(ctx, OT_ECUDA, "multi-solve kernel: %zu bytes of shared memory refused", smem);
     }
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk.solve, 32 * (kk.ncw + 1), smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk.solve, kk.nthreads, smem) != cudaSuccess ||
         occ < 1 || grid > occ * ctx->num_sms) {
         cudaGetLastError();
         return set_error(ctx, OT_EUNSUPPORTED, "multi-solve kernel cannot be resident");
@@ -619,7 +620,7 @@ ot_status launch_solve_multi(ot_assoc_ctx* ctx, const SolveArgs& a, int n, const
     timing_mark(ctx, 1, s);
     {
         void* args[] = {&M, &S};
-        e = cudaLaunchCooperativeKernel(kk.solve, dim3(grid), dim3(32 * (kk.ncw + 1)), args, smem, s);
+        e = cudaLaunchCooperativeKernel(kk.solve, dim3(grid), dim3(kk.nthreads), args, smem, s);
         if (e != cudaSuccess) return cuda_error(ctx, e, "multi-solve launch");
     }
     timing_mark(ctx, 2, s);
