@@ -151,6 +151,23 @@ def stored_traffic():
     return float(m_t.group(1))
 
 
+EUCLID_PROFILE = os.path.join(ROOT, "profiles", "sk_solve_euclid_50000x800.md")
+
+
+def stored_euclid_inst():
+    """Warp instructions per cell and sweep of sk_solve_euclid from the committed ncu summary,
+    or None when it is missing or was taken on other solver sources than the ones built now."""
+    try:
+        text = open(EUCLID_PROFILE).read()
+    except OSError:
+        return None
+    m_i = re.search(r"^warp_inst_per_cell_sweep:\s*([0-9.eE+]+)", text, re.M)
+    m_h = re.search(r"^solver_source_sha256:\s*([0-9a-f]+)", text, re.M)
+    if not m_i or not m_h or m_h.group(1) != solver_source_hash():
+        return None
+    return float(m_i.group(1))
+
+
 def make_inputs():
     from paper_1805_01559_gb300 import instances
     return instances.config2(seed=0)
@@ -893,8 +910,17 @@ def run_euclid(args):
     ms = statistics.median(ms_f)
     ci = float(I) * J * sum(its)
     # two SFU operations a cell and sweep (the exponential and the square root's reciprocal
-    # square root): 152 SMs x 16 SFU results a clock x 2.07 GHz / 2
-    peak_cells = 152 * 16 * 2.07e9 / 2
+    # square root): 152 SMs x 16 SFU results a clock x 2.07 GHz / 2; and the issue bound of
+    # the kernel's instruction mix: 152 SMs x 4 schedulers x 1 warp instruction a clock x
+    # 2.07 GHz / (warp instructions per cell and sweep, counted by ncu).  The lower binds.
+    sfu_cells = 152 * 16 * 2.07e9 / 2
+    wi = stored_euclid_inst()
+    issue_cells = 152 * 4 * 2.07e9 / wi if wi else None
+    if issue_cells and issue_cells < sfu_cells:
+        peak_cells, peak_kind = issue_cells, (f"derived: issue bound, 152 SMs x 4 warp instructions/clk x 2.07 GHz / "
+                                              f"{wi:.4f} warp instructions per cell and sweep (ncu count)")
+    else:
+        peak_cells, peak_kind = sfu_cells, "derived: 152 SMs x 16 SFU/clk x 2.07 GHz / 2 SFU ops per cell"
     sweeps = sum(it + 2 for it in its)
     achieved = float(I) * J * sweeps / (ms / 1e3)
     line = {"metric": METRIC, "value": ci / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -905,10 +931,10 @@ def run_euclid(args):
                        "l2": "no matrix is read"},
             "materialized": {"ms": statistics.median(ms_m), "iters": its_m,
                              "cells_iters_per_s": float(I) * J * sum(its_m) / (statistics.median(ms_m) / 1e3)},
-            "roofline": {"bound": "alu", "kernel": "sk_solve_euclid (SFU: ex2 and the square root per cell)",
+            "roofline": {"bound": "alu", "kernel": "sk_solve_euclid (cost, ex2 and the square root formed per cell)",
                          "achieved": achieved, "peak": peak_cells, "unit": "cells*sweeps/s",
-                         "frac": achieved / peak_cells, "traffic": None,
-                         "peak_kind": "derived: 152 SMs x 16 SFU/clk x 2.07 GHz / 2 SFU ops per cell"},
+                         "frac": achieved / peak_cells, "traffic": None, "peak_kind": peak_kind,
+                         "sfu_bound": sfu_cells, "issue_bound": issue_cells},
             "gpu_launches": launches, "clocks": clk}
     ctx.close()
     print(json.dumps(line), flush=True)
