@@ -78,3 +78,14 @@ def test_stored_traffic_follows_the_solver_sources(tmp_path, monkeypatch):
     assert bench.stored_traffic() is None
     monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(tmp_path / "missing.md"))
     assert bench.stored_traffic() is None
+
+
+def test_stored_euclid_instruction_count_follows_the_solver_sources(tmp_path, monkeypatch):
+    f = tmp_path / "e.md"
+    f.write_text(f"x\nwarp_inst_per_cell_sweep: 1.25\nsolver_source_sha256: {bench.solver_source_hash()}\n")
+    monkeypatch.setattr(bench, "EUCLID_PROFILE", str(f))
+    assert bench.stored_euclid_inst() == 1.25
+    f.write_text("warp_inst_per_cell_sweep: 1.25\nsolver_source_sha256: 0123456789abcdef\n")
+    assert bench.stored_euclid_inst() is None
+    monkeypatch.setattr(bench, "EUCLID_PROFILE", str(tmp_path / "missing.md"))
+    assert bench.stored_euclid_inst() is None
