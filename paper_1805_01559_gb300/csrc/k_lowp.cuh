@@ -514,7 +514,7 @@ template <typename T>
 bool lp_pick(int J, LpKernel* k) {
     constexpr int N = Chunk<T>::N;
     const int Jc = (J + N - 1) / N;
-    if (N == 4) {
+    if constexpr (N == 4) {
         if (Jc <= 32) *k = lp_kernel<T, 1, 1>();
         else if (Jc <= 64) *k = lp_kernel<T, 1, 2>();
         else if (Jc <= 128) *k = lp_kernel<T, 1, 4>();
