@@ -392,6 +392,9 @@ ot_status ot_assoc_batch_launch(ot_assoc_batch* b, void* stream);
 /* Synchronise `stream` and fill res[0..n) [host] (res may be NULL). */
 ot_status ot_assoc_batch_wait(ot_assoc_batch* b, void* stream, ot_assoc_instance_result* res);
 
+/* Free the batch's graph, descriptors and scratch.  Call it with no launch of the batch
+ * running (after ot_assoc_batch_wait).  NULL is a no-op.  Destroy batches before their
+ * context. */
 void ot_assoc_batch_destroy(ot_assoc_batch* b);
 
 /* Autotune the tuning table on a batch: bucket by bucket, time the whole batch (iters
@@ -408,6 +411,9 @@ ot_status ot_assoc_autotune(ot_assoc_ctx* ctx, const ot_assoc_instance* inst, in
  * bit in any batch. */
 ot_status ot_assoc_tuning_get(const ot_assoc_ctx* ctx, int32_t bucket, int32_t* gsize,
                               int32_t* stage_bytes, double* rate);
+/* Set bucket's entry: gsize 0 or a divisor of the SM count, stage_bytes >= 0 (0: 24 KB);
+ * OT_EINVAL otherwise (or for a bucket outside [0, 15)).  Applies to batches planned
+ * afterwards. */
 ot_status ot_assoc_tuning_set(ot_assoc_ctx* ctx, int32_t bucket, int32_t gsize, int32_t stage_bytes);
 /* Size bucket of an I x J instance. */
 int32_t ot_assoc_bucket(int64_t I, int32_t J);
@@ -580,6 +586,9 @@ typedef struct {
     uint64_t launches;
 } ot_assoc_server_stats_t;
 
+/* Create a server on ctx's device (cfg NULL: the defaults above); *out [host] gets the
+ * handle.  OT_EINVAL when group_ctas does not divide the SM count or out is NULL,
+ * OT_EUNSUPPORTED when max_J is above 1024. */
 ot_status ot_assoc_server_create(ot_assoc_ctx* ctx, const ot_assoc_server_config* cfg, ot_assoc_server** out);
 /* Waits for work in flight, frees everything.  Destroy before the context. */
 void ot_assoc_server_destroy(ot_assoc_server* s);
@@ -598,6 +607,8 @@ ot_status ot_assoc_server_drain(ot_assoc_server* s, double timeout_s);
  * between requests of that cell). */
 ot_status ot_assoc_server_cell_state(const ot_assoc_server* s, int32_t cell, const float** C, double** f,
                                      double** g, double** rrh_load);
+/* Counters of the server [host]: resident bytes, cells, groups, requests waiting and in
+ * flight, persistent launches so far. */
 ot_status ot_assoc_server_stats(const ot_assoc_server* s, ot_assoc_server_stats_t* out);
 /* The eps a cell solves with [host]. */
 ot_status ot_assoc_server_cell_eps(const ot_assoc_server* s, int32_t cell, double* eps);
