@@ -941,6 +941,73 @@ def run_euclid(args):
     return 0
 
 
+def run_epsscale(args):
+    """eps-scaling on the 50,000 x 800 step's instance: Algorithm 1 at eps = 0.01 x median(C)
+    from b = 1 (sk_solve) against the same eps reached through the stages 0.1 -> 0.03 ->
+    0.01 x median (sk_eps_scaling, one launch, each stage warm-started from the previous
+    stage's g, intermediate stages to tol 1e-3, the last to the step's tol)."""
+    import torch
+
+    from paper_1805_01559_gb300 import binding
+    inst = make_inputs()
+    I, J = inst.I, inst.J
+    dev = torch.device("cuda", 0)
+    ctx = binding.Context(0)
+    G = torch.from_numpy(np.ascontiguousarray(inst.G, dtype=np.float32)).to(dev)
+    P = torch.from_numpy(inst.P.astype(np.float32)).to(dev)
+    lam = torch.from_numpy(inst.lam.astype(np.float32)).to(dev)
+    q = torch.from_numpy(inst.q.astype(np.float32)).to(dev)
+    C, med = ctx.build_cost_from_gains(G, P, inst.N0, inst.W_hz, inst.mu, eps_rel=1.0)
+    eps, eps0, factor = 0.01 * med, 0.1 * med, 0.3
+    s = torch.cuda.current_stream()
+
+    def direct():
+        r = ctx.solve_cost(C, lam, q, eps, tol=TOL, max_iter=MAX_ITER)
+        return [r.iters], r.transport_cost
+
+    def staged():
+        r, stages = ctx.solve_eps_scaling(C, lam, q, eps, eps0, factor=factor, tol_stage=1e-3, tol=TOL,
+                                          max_iter=MAX_ITER)
+        return stages, r.transport_cost
+
+    for _ in range(args.warmup):
+        direct()
+        staged()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = ctx.launch_count()
+    out = {}
+    for name, fn in (("direct", direct), ("eps_scaling", staged)):
+        ms_all, its, cost = [], None, None
+        for _ in range(args.steps):
+            (its, cost), ms, _ = _timed(fn, s)
+            ms_all.append(ms)
+        ms = statistics.median(ms_all)
+        sweeps = sum(it + 2 for it in its)  # each stage: its iterations, the first and the finalize sweep
+        out[name] = {"ms": ms, "iters": its, "transport_cost": cost,
+                     "hbm_gbs": 4.0 * I * J * sweeps / (ms / 1e3) / 1e9}
+    launches = (ctx.launch_count() - l0) / (2 * args.steps)
+    clk = clocks.stop()
+    peak, peak_kind = _peaks()
+    st = out["eps_scaling"]
+    line = {"metric": METRIC, "value": float(I) * J * sum(st["iters"]) / (st["ms"] / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": st["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "epsscale_50000x800: eps = 0.01 x median(C), direct vs stages 0.1 -> 0.03 -> 0.01",
+                       "I": I, "J": J, "tol": TOL, "tol_stage": 1e-3, "factor": factor,
+                       "l2": "inputs larger than L2 (C 160 MB)"},
+            "solves": out,
+            "speedup_vs_direct": out["direct"]["ms"] / st["ms"],
+            "roofline": {"bound": "hbm", "kernel": "sk_eps_scaling (whole call, CUDA events on its stream)",
+                         "achieved": st["hbm_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": st["hbm_gbs"] / peak, "traffic": None, "peak_kind": peak_kind,
+                         "reads_of_C_per_launch": "sum over stages of (iters + 2)"},
+            "gpu_launches": launches, "clocks": clk}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -953,7 +1020,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=12_500)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="only run this many rounds of the three solves of one step (for profiler captures)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2", "policies", "euclid"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2", "policies", "euclid", "epsscale"],
                     help="c2: the headline line; c3 batched ragged; c4 stored-kernel precision; c5 serving; "
                          "alg2 adaptive association (Algorithm 2)")
     ap.add_argument("--alg2-outer", type=int, default=20)
@@ -969,7 +1036,7 @@ def main():
         return run_profile_solve(args)
     if args.workload != "c2" and args.impl != "reference":
         return {"c3": run_c3, "c4": run_c4, "c5": run_c5, "alg2": run_alg2,
-                "policies": run_policies, "euclid": run_euclid}[args.workload](args)
+                "policies": run_policies, "euclid": run_euclid, "epsscale": run_epsscale}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
