@@ -49,19 +49,48 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """SM clocks and throttle reasons sampled while the timed region runs.
+
+    Reads NVML through ctypes every 10 ms (the timed region can be shorter than
+    nvidia-smi's shortest interval); falls back to `nvidia-smi -lms 200` when NVML cannot be
+    loaded.  Only reads: no clock, power or other setting is changed."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clocks-event reason bits
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+               "hw_thermal_slowdown": 0x40}
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, period_s: float = 0.01):
         self.dev = device_index
+        self.period = period_s
         self.proc = None
         self.lines = []
+        self.samples = []  # (sm_mhz, max_mhz, reason bits) from NVML
         self.t = None
+        self._halt = threading.Event()
+        self._nvml = None
+
+    def _nvml_open(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return None
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.dev), ctypes.byref(h)) != 0:
+            return None
+        return lib, h
 
     def start(self):
+        self._nvml = self._nvml_open()
+        if self._nvml is not None:
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -72,11 +101,34 @@ class ClockSampler:
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
 
+    def _poll(self):
+        import ctypes
+        lib, h = self._nvml
+        mhz, mx = ctypes.c_uint(), ctypes.c_uint()
+        bits = ctypes.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._halt.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    get_reasons(h, ctypes.byref(bits)) == 0):
+                self.samples.append((float(mhz.value), float(mx.value), int(bits.value)))
+            self._halt.wait(self.period)
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self._nvml is not None:
+            self._halt.set()
+            self.t.join(timeout=2)
+            if not self.samples:
+                return None
+            reasons = sorted(nm for nm, bit in self.REASONS.items() if any(b & bit for _, _, b in self.samples))
+            return {"sm_mhz": statistics.median(x[0] for x in self.samples),
+                    "sm_max_mhz": max(x[1] for x in self.samples), "reasons": reasons,
+                    "samples": len(self.samples), "source": "nvml, 10 ms"}
         if not self.proc:
             return None
         self.proc.terminate()
@@ -103,7 +155,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 def _dist():
@@ -233,6 +285,36 @@ def run_reference(args):
     return 0
 
 
+def solve_roofline(per_launch, I: int, J: int, peak: float):
+    """Roofline of the solver over a step's launches.
+
+    per_launch[k] lists (kernel ms, iterations, completed sweeps) of every timed launch of the
+    k-th eps.  The algorithmic bytes of a launch are 4 B x I x J x iterations (one read of C per
+    iteration of Algorithm 1); achieved = their sum over all launches / the summed kernel
+    time.  The same with the two extra reads the kernel makes (testing the last plan, the
+    finalize sweep) is reported apart as frac_incl_setup_finalize."""
+    launches = [x for lst in per_launch for x in lst]
+    if not launches:
+        return {"achieved": None, "alg_bytes_per_launch": None, "frac_incl_setup_finalize": None,
+                "per_launch": [], "launches_timed": 0}
+    cell = 4.0 * I * J
+    ms = sum(x[0] for x in launches)
+    alg = sum(cell * x[1] for x in launches)
+    reads = sum(cell * (x[2] + 2) for x in launches)
+    rows = []
+    for lst in per_launch:
+        if not lst:
+            continue
+        lms = sum(x[0] for x in lst) / len(lst)
+        it = sum(x[1] for x in lst) / len(lst)
+        gbs = cell * it / 1e9 / (lms / 1e3)
+        rows.append({"iters": it, "ms": lms, "achieved": gbs, "frac": gbs / peak,
+                     "frac_incl_setup_finalize": cell * (it + 2) / 1e9 / (lms / 1e3) / peak})
+    return {"achieved": alg / 1e9 / (ms / 1e3), "alg_bytes_per_launch": alg / len(launches),
+            "frac_incl_setup_finalize": reads / 1e9 / (ms / 1e3) / peak, "per_launch": rows,
+            "launches_timed": len(launches)}
+
+
 # ------------------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -261,7 +343,8 @@ def run_gpu(args):
     gs = [torch.empty(J, dtype=torch.float64, device=dev) for _ in EPS_REL]
     ctx = binding.Context(local)
     ctx.enable_timing(True)
-    loop_ms, loop_bytes = [], []
+    # per eps: (kernel ms, iterations, completed sweeps) of every timed launch
+    per_launch = [[] for _ in EPS_REL]
     iters_seen = []
 
     def step(record=False, buf=None):
@@ -269,9 +352,18 @@ def run_gpu(args):
         # rates (Sec. II-A) and the cost in one pass over the gains, then the median of C
         _, med = ctx.build_cost_from_gains(G, P, inst.N0, inst.W_hz, inst.mu, eps_rel=1.0, C_out=C)
         if not args.multi:
-            # the three solves enqueued back to back, each reading C on its own
-            results = [x.wait() for x in [ctx.solve_cost_async(C, lam, q, er * med, tol=TOL, max_iter=MAX_ITER,
-                                                               f=fs[k], g=gs[k]) for k, er in enumerate(EPS_REL)]]
+            # the three solves enqueued back to back, each reading C on its own; each solve's
+            # kernel timing is read right after its own wait (the next wait replaces it)
+            tickets = [ctx.solve_cost_async(C, lam, q, er * med, tol=TOL, max_iter=MAX_ITER, f=fs[k], g=gs[k])
+                       for k, er in enumerate(EPS_REL)]
+            results = []
+            for k, x in enumerate(tickets):
+                res = x.wait()
+                results.append(res)
+                if record:
+                    t = ctx.last_timings()
+                    if t["valid"]:
+                        per_launch[k].append((t["loop_ms"], res.iters, t["sweeps"]))
         else:
             # the first eps on its own launch, the two smaller ones in one launch sharing each
             # read of C while both iterate
@@ -280,8 +372,7 @@ def run_gpu(args):
             if record:
                 t = ctx.last_timings()
                 if t["valid"]:
-                    loop_ms.append(t["loop_ms"])
-                    loop_bytes.append(4.0 * I * J * (t["sweeps"] + 2))
+                    per_launch[0].append((t["loop_ms"], r0.iters, t["sweeps"]))
             results = [r0] + ctx.solve_cost_multi(C, lam, q, [er * med for er in EPS_REL[1:]], tol=TOL,
                                                   max_iter=MAX_ITER, fs=fs[1:], gs=gs[1:])
         cells = 0
@@ -289,19 +380,10 @@ def run_gpu(args):
         for res in results:
             cells += I * J * res.iters
             its.append(res.iters)
-            if record and not args.multi:
-                t = ctx.last_timings()
-                if t["valid"]:
-                    # the persistent kernel reads C once per iteration, once more to test the
-                    # last plan, and once in the finalize sweep
-                    loop_ms.append(t["loop_ms"])
-                    loop_bytes.append(4.0 * I * J * (t["sweeps"] + 2))
         if record and args.multi:
             t = ctx.last_timings()
             if t["valid"]:
-                # one launch reads C max(iters) + 2 n times (timings report that as sweeps + 2)
-                loop_ms.append(t["loop_ms"])
-                loop_bytes.append(4.0 * I * J * (t["sweeps"] + 2))
+                per_launch[1].append((t["loop_ms"], sum(r.iters for r in results[1:]), t["sweeps"]))
         return cells, its
 
     for _ in range(args.warmup):
@@ -372,7 +454,7 @@ def run_gpu(args):
     d2h = sum(x.numel() * 8 for x in f_h) + sum(x.numel() * 8 for x in g_h)
 
     peak, peak_kind = _peaks()
-    achieved = (sum(loop_bytes) / 1e9) / (sum(loop_ms) / 1e3) if loop_ms else None
+    roof = solve_roofline(per_launch, I, J, peak)
     traffic = stored_traffic()
     if rank == 0:
         line = {
@@ -389,14 +471,18 @@ def run_gpu(args):
                                     if not args.multi else
                                     "sk_solve for the first eps, sk_solve_multi for the other two (first and "
                                     "finalize sweeps one solve after the other, plan-scale sweeps shared)"),
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "achieved": roof["achieved"], "peak": peak, "unit": "GB/s",
+                         "frac": (roof["achieved"] / peak) if roof["achieved"] else None, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "bytes_per_cell_iter": 4,
+                         "definition": "4 B x I x J x iterations, summed over the step's solver launches, / "
+                                       "their summed kernel time (CUDA events on the solve stream)",
+                         "alg_bytes_per_launch": roof["alg_bytes_per_launch"],
+                         "frac_incl_setup_finalize": roof["frac_incl_setup_finalize"],
                          "reads_of_C_per_launch": "iters + 2" if not args.multi else
                          "iters + 2, then max(iters) + 2 x 2",
-                         "alg_bytes_per_launch": (sum(loop_bytes) / len(loop_bytes)) if loop_bytes else None,
-                         "launches_timed": len(loop_ms)},
+                         "per_launch": roof["per_launch"],
+                         "launches_timed": roof["launches_timed"]},
             "e2e": {"value": e2e_cells / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -31,7 +31,10 @@
  *     residual" of Sec. III-C): after each full iteration k (a-update then
  *     b-update) the row residual of pi^(k) is compared with `tol`; the loop ends at
  *     the first k with residual <= tol, or at k = max_iter (status
- *     OT_NOT_CONVERGED, results still valid).
+ *     OT_NOT_CONVERGED, results still valid).  The FP32 solvers form that residual
+ *     from FP32 cell values and stop at residual <= tol (1 - 2^-5): the FP32 figure
+ *     sits within about 1e-8 of the exact residual of the returned potentials, so the
+ *     returned plan's exact FP64 residual stays <= tol.
  */
 #ifndef OT_ASSOC_H
 #define OT_ASSOC_H
@@ -258,12 +261,16 @@ ot_status ot_assoc_wait(ot_assoc_ctx* ctx, uint64_t ticket, ot_assoc_result* out
  * arguments, outputs, stopping rule and status codes as ot_assoc_solve_cost; error
  * messages are not recorded (there is no context), only the status code.
  *
- * The first call on a device looks up the array's device address with that device
- * current (cudaGetSymbolAddress), once; make that first call before any stream capture.
+ * Every call looks up the array's device address in the current device's context
+ * (cudaGetSymbolAddress, which allocates nothing), so the entry point keeps working after
+ * the context is destroyed and re-created.  The first call on a device may load the
+ * library's device code into that context: make it before any stream capture.
  * Every call on a device shares the one array and overwrites what the previous call left
  * there (the state words are cleared at the start of each call): calls whose GPU work
  * overlaps -- on different streams or from different threads -- race and give wrong
- * results.  Synchronises the stream before returning.
+ * results, or return OT_ETIMEOUT after the fixed limit of 2^24 polls of a grid barrier
+ * (one call's clearing of the state words can reset another call's barrier counters).
+ * Synchronises the stream before returning.
  */
 ot_status ot_assoc_solve_cost_noalloc(const float* C, int64_t ld_c, const float* p, const float* q,
                                       int64_t I, int64_t J, double eps, double tol, int32_t max_iter,
@@ -585,6 +592,28 @@ typedef struct {
     int32_t cells, groups, group_ctas, waiting, inflight, reserved;
     uint64_t launches;
 } ot_assoc_server_stats_t;
+
+/*
+ * One time instance of a drifting cell, built the way the server rebuilds it inside its
+ * kernel, for callers that solve instances one by one (ot_assoc_solve_cost) instead of
+ * serving them: every device moves dt seconds along its velocity and reflects at the walls
+ * of [0, side_m]^2 (dev_xy and dev_v are updated in place), its gains follow the path-loss
+ * model PL = 30 dB + 35 log10(max(d, 10 m)) with the link's fixed shadowing (FP32, evaluated
+ * as 2^(a - 1.75 log2 d^2): a simulation input), then the rates with every other RRH
+ * interfering (Sec. II-A) and C = 1 / (mu R) (Sec. IV choice (ii)).
+ * dev_xy, dev_v [device] double I x 2 (m, m/s); rrh_xy [device] float J x 2 (m);
+ * shadow_db [device] float I x J (dB, row-major, ld = J); P [device] float J (W);
+ * C_out [device] float I x J (ld_c, 0 = J).
+ * Without eps_out the call only enqueues, and a rate that comes out non-positive or not
+ * finite leaves C_ij = +inf (a link the plan cannot use).  With eps_out [host] it also sets
+ * *eps_out = eps_rel * median(C), synchronises the stream, and returns OT_EINVAL when any
+ * rate was invalid.  OT_EINVAL for null pointers, I or J <= 0, dt < 0, side_m <= 0,
+ * N0 < 0, W_hz <= 0 or mu <= 0.
+ */
+ot_status ot_assoc_build_cost_mobile(ot_assoc_ctx* ctx, double* dev_xy, double* dev_v, const float* rrh_xy,
+                                     const float* shadow_db, const float* P, int64_t I, int64_t J, double dt,
+                                     double side_m, double N0, double W_hz, double mu, float* C_out, int64_t ld_c,
+                                     double eps_rel, double* eps_out, void* stream);
 
 /* Create a server on ctx's device (cfg NULL: the defaults above); *out [host] gets the
  * handle.  OT_EINVAL when group_ctas does not divide the SM count or out is NULL,

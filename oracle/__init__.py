@@ -45,6 +45,7 @@ def _load():
         i64, i32 = ctypes.c_int64, ctypes.c_int32
         pi32 = ctypes.POINTER(ctypes.c_int32)
         lib.oracle_rates.argtypes = [d, d, i64, i64, ctypes.c_double, ctypes.c_double, d]
+        lib.oracle_rates_total.argtypes = [d, d, i64, i64, ctypes.c_double, ctypes.c_double, d]
         lib.oracle_cost.argtypes = [d, i64, ctypes.c_double, d]
         lib.oracle_median.argtypes = [d, i64, d]
         lib.oracle_sinkhorn.argtypes = [d, d, d, i64, i64, ctypes.c_double, ctypes.c_double, i32,
@@ -58,7 +59,7 @@ def _load():
         lib.oracle_euclid_cost.argtypes = [d, d, i64, i64, d]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
-        for name in ("oracle_rates", "oracle_cost", "oracle_median", "oracle_sinkhorn",
+        for name in ("oracle_rates", "oracle_rates_total", "oracle_cost", "oracle_median", "oracle_sinkhorn",
                      "oracle_plan", "oracle_finalize", "oracle_maxsinr", "oracle_adaptive",
                      "oracle_completion", "oracle_euclid_cost"):
             getattr(lib, name).restype = ctypes.c_int
@@ -93,6 +94,15 @@ def rates(G, P, N0: float, W_hz: float) -> np.ndarray:
     I, J = G.shape
     R = np.empty((I, J))
     _check(_load().oracle_rates(_dp(G), _dp(P), I, J, float(N0), float(W_hz), _dp(R)), "rates")
+    return R
+
+
+def rates_total(G, P, N0: float, W_hz: float) -> np.ndarray:
+    """rates() with the interference as row total minus own term (O(I J)), Sec. II-A."""
+    G, P = _f64(G), _f64(P)
+    I, J = G.shape
+    R = np.empty((I, J))
+    _check(_load().oracle_rates_total(_dp(G), _dp(P), I, J, float(N0), float(W_hz), _dp(R)), "rates_total")
     return R
 
 

@@ -18,11 +18,13 @@
  * Parity status of each function (see the tests for the pins):
  *   oracle_rates      pinned (single-RRH closed form, symmetric two-RRH case,
  *                     low-SINR limit)
+ *   oracle_rates_total pinned (equal to oracle_rates on random and dominant-link rows)
  *   oracle_cost       pinned (closed form)
  *   oracle_median     pinned (arange closed form, library select)
  *   oracle_sinkhorn   pinned (J = 1, separable cost, 2x2 closed form, scaling-
  *                     domain brute force, LP limit, Lemma 1 bounds, invariants)
- *   oracle_finalize   pinned (marginals of closed-form plans)
+ *   oracle_finalize   pinned (marginals of closed-form plans; residuals per unit
+ *                     mass on a perturbed product plan of mass 3)
  *   oracle_maxsinr    pinned (brute-force argmax, Lemma 1)
  *   oracle_adaptive   pinned (one outer step by hand, mass conservation)
  *   oracle_completion pinned (hand-worked two-device cases, overload -> inf)
@@ -76,6 +78,36 @@ int oracle_rates(const double* G, const double* P, int64_t I, int64_t J, double 
                 if (k != j) interference += P[k] * g[k];
             double sinr = P[j] * g[j] / interference;
             R_out[i * J + j] = W * log1p(sinr) / log(2.0);
+        }
+    }
+    return ORC_OK;
+}
+
+/*
+ * The same rates with the interference formed as the row total minus the own term:
+ *   I_ij = sum_k P_k G_ik - P_j G_ij + N_0,
+ * O(I J) instead of O(I J^2), for instances too large for the direct sum.  The row total
+ * is a compensated (Neumaier) sum, so T - P_j G_ij loses no more than the rounding of T
+ * itself; both formulations agree to FP64 rounding wherever the own term does not carry
+ * all but ~1e-10 of the row total.
+ */
+int oracle_rates_total(const double* G, const double* P, int64_t I, int64_t J, double N0, double W,
+                       double* R_out) {
+    if (I <= 0 || J <= 0 || !(N0 >= 0.0) || !(W > 0.0)) return ORC_EINVAL;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < I; ++i) {
+        const double* g = G + i * J;
+        double t = 0.0, c = 0.0;
+        for (int64_t k = 0; k < J; ++k) {
+            const double x = P[k] * g[k];
+            const double u = t + x;
+            c += fabs(t) >= fabs(x) ? (t - u) + x : (x - u) + t;
+            t = u;
+        }
+        for (int64_t j = 0; j < J; ++j) {
+            const double own = P[j] * g[j];
+            const double interference = ((t - own) + c) + N0;
+            R_out[i * J + j] = W * log1p(own / interference) / log(2.0);
         }
     }
     return ORC_OK;

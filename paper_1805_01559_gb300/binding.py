@@ -1030,3 +1030,38 @@ def _ctx_build_cost_from_gains(self, G, P, N0, W_hz, mu, eps_rel=None, C_out=Non
 
 
 Context.build_cost_from_gains = _ctx_build_cost_from_gains
+
+
+# ---- one time instance of a drifting cell -----------------------------------------------------------
+SIGNATURES["ot_assoc_build_cost_mobile"] = (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _I64, _I64, _D, _D, _D,
+                                                           _D, _D, _VP, _I64, _D, _PD, _VP])
+if _lib is not None:
+    _lib.ot_assoc_build_cost_mobile.restype, _lib.ot_assoc_build_cost_mobile.argtypes = \
+        SIGNATURES["ot_assoc_build_cost_mobile"]
+
+
+def _ctx_build_cost_mobile(self, dev_xy, dev_v, rrh_xy, shadow_db, P, dt, side_m, N0, W_hz, mu, C_out=None,
+                           eps_rel=None, stream=None):
+    """Move the devices by dt (dev_xy, dev_v updated in place) and rebuild C (rates of Sec. II-A,
+    cost of Sec. IV); returns (C, eps or None)."""
+    _need(dev_xy, torch.float64, "dev_xy", 2)
+    _need(dev_v, torch.float64, "dev_v", 2)
+    _need(rrh_xy, torch.float32, "rrh_xy", 2)
+    _need(shadow_db, torch.float32, "shadow_db", 2)
+    _need(P, torch.float32, "P", 1)
+    I, J = shadow_db.shape
+    if (dev_xy.shape != (I, 2) or dev_v.shape != (I, 2) or rrh_xy.shape != (J, 2) or P.shape[0] != J
+            or not all(t.is_contiguous() for t in (dev_xy, dev_v, rrh_xy, shadow_db))):
+        raise ValueError("dev_xy, dev_v (I, 2), rrh_xy (J, 2), shadow_db (I, J) contiguous, P (J,)")
+    if C_out is None:
+        C_out = torch.empty((I, J), dtype=torch.float32, device=shadow_db.device)
+    _need(C_out, torch.float32, "C_out", 2)
+    eps = ctypes.c_double(0.0)
+    self._check(self._L.ot_assoc_build_cost_mobile(
+        self._h, _ptr(dev_xy), _ptr(dev_v), _ptr(rrh_xy), _ptr(shadow_db), _ptr(P), I, J, float(dt), float(side_m),
+        float(N0), float(W_hz), float(mu), _ptr(C_out), C_out.stride(0), float(eps_rel or 0.0),
+        ctypes.byref(eps) if eps_rel is not None else None, _stream(stream)))
+    return C_out, (eps.value if eps_rel is not None else None)
+
+
+Context.build_cost_mobile = _ctx_build_cost_mobile

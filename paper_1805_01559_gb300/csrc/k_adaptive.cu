@@ -225,7 +225,7 @@ ot_status ot_assoc_adaptive(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, con
     const size_t o_rho = off;
     off = al(off + sizeof(double) * Jp);
     const size_t o_grp = off;
-    const size_t gbytes = 1024 + al(3 * (size_t)Jp * 8) + al((size_t)V * 2 * Jp * 4) + al((size_t)V * 16) +
+    const size_t gbytes = 1024 + al(gstate_bytes(Jp)) + al((size_t)V * 2 * Jp * 4) + al((size_t)V * 16) +
                           al((size_t)V * Jp * 16) + al((size_t)grid * BT_NW * 16 + (size_t)V * 8);
     off = al(off + gbytes);
     ot_status st = OT_OK;
@@ -262,7 +262,7 @@ ot_status ot_assoc_adaptive(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, con
     A.grp.ls = (LoopState*)(gb + 512);
     size_t o = 1024;
     A.grp.G = (double*)(gb + o);
-    o += al(3 * (size_t)Jp * 8);
+    o += al(gstate_bytes(Jp));
     A.grp.colpart = (float*)(gb + o);
     o += al((size_t)V * 2 * Jp * 4);
     A.grp.errpart = (double*)(gb + o);

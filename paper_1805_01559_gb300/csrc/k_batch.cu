@@ -373,7 +373,7 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
     for (int gi = 0; gi < ngroups_total; ++gi) {
         const size_t Jp = phase_jp[gplan[gi].phase], nb = (size_t)b->h_phases[gplan[gi].phase].gsize;
         const size_t nv = phase_v[gplan[gi].phase];
-        const size_t bytes = 1024 + al(3 * Jp * 8) + al(nv * 2 * Jp * 4) + al(nv * 16) + al(nv * Jp * 16) +
+        const size_t bytes = 1024 + al(gstate_bytes((int)Jp)) + al(nv * 2 * Jp * 4) + al(nv * 16) + al(nv * Jp * 16) +
                              al(nb * BT_NW * 16 + nv * 8);
         g_off[gi] = off;
         off = al(off + bytes);
@@ -409,7 +409,7 @@ static ot_status batch_plan(ot_assoc_batch* b, int forced_gsize, int forced_stag
         G.ls = (LoopState*)(g + 512);
         size_t o = 1024;
         G.G = (double*)(g + o);
-        o += al(3 * Jp * 8);
+        o += al(gstate_bytes((int)Jp));
         G.colpart = (float*)(g + o);
         o += al(nv * 2 * Jp * 4);
         G.errpart = (double*)(g + o);

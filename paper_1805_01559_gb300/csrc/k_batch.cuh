@@ -38,7 +38,7 @@ struct BRes {
 struct BGroup {
     DevScalars* sc;
     LoopState* ls;
-    double* G;         // [3][Jp]
+    double* G;         // gstate_words(Jp)
     float* colpart;    // [V][2 * Jp]
     double* errpart;   // [V] (x2)
     double2* fpart;    // [V][Jp] finalize column partials

@@ -145,7 +145,7 @@ ot_status ot_assoc_solve_eps_scaling(ot_assoc_ctx* ctx, const float* C, int64_t 
     const size_t o_st = off;
     off = al(off + sizeof(EsStage) * ns);
     const size_t o_grp = off;
-    const size_t gbytes = 1024 + al(3 * (size_t)Jp * 8) + al((size_t)V * 2 * Jp * 4) + al((size_t)V * 16) +
+    const size_t gbytes = 1024 + al(gstate_bytes(Jp)) + al((size_t)V * 2 * Jp * 4) + al((size_t)V * 16) +
                           al((size_t)V * Jp * 16) + al((size_t)grid * BT_NW * 16 + (size_t)V * 8);
     off = al(off + gbytes);
     ot_status st = OT_OK;
@@ -182,7 +182,7 @@ ot_status ot_assoc_solve_eps_scaling(ot_assoc_ctx* ctx, const float* C, int64_t 
     A.grp.ls = (LoopState*)(gb + 512);
     size_t o = 1024;
     A.grp.G = (double*)(gb + o);
-    o += al(3 * (size_t)Jp * 8);
+    o += al(gstate_bytes(Jp));
     A.grp.colpart = (float*)(gb + o);
     o += al((size_t)V * 2 * Jp * 4);
     A.grp.errpart = (double*)(gb + o);

@@ -131,8 +131,13 @@ __global__ void __launch_bounds__(256) lp_build(const float* __restrict__ C, int
                                                 const double* __restrict__ G, float2* Fref, double* Gref,
                                                 float k_hi, float k_lo) {
     constexpr int N = Chunk<T>::N;
-    extern __shared__ float Gs_build[];
-    for (int j = threadIdx.x; j < Jp; j += blockDim.x) Gs_build[j] = j < J ? (float)G[j] : 0.f;
+    extern __shared__ float Gs_build[];  // G as FP32 pairs: high parts, then low parts
+    for (int j = threadIdx.x; j < Jp; j += blockDim.x) {
+        const double x = j < J ? G[j] : 0.0;
+        const float hi = (float)x;
+        Gs_build[j] = hi;
+        Gs_build[Jp + j] = (float)(x - (double)hi);
+    }
     if (blockIdx.x == 0)
         for (int j = threadIdx.x; j < Jp; j += blockDim.x) Gref[j] = G[j];
     __syncthreads();
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(256) lp_build(const float* __restrict__ C, int
 #pragma unroll
             for (int e = 0; e < N; ++e) {
                 const int j = ch * N + e;
-                v[e] = j < J ? ex2(expo(Fi.x, Fi.y + Gs_build[j], __ldg(row + j), k_hi, k_lo)) : 0.f;
+                v[e] = j < J ? ex2(expo2(Fi.x, Fi.y + Gs_build[Jp + j], Gs_build[j], __ldg(row + j), k_hi, k_lo)) : 0.f;
             }
             Chunk<T>::store(out + (int64_t)ch * N, v);
         }
@@ -398,12 +403,12 @@ __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg&
             e = warp_sum_df(e);
             if (lane == 0) {
                 const double ed = (double)e.x + (double)e.y;
-                const int stop = (ed <= P.tol) || (s - 1 >= P.max_iter) || ld_volatile_i32(status) != DEV_OK;
+                const int stop = (ed <= stop_tol(P.tol)) || (s - 1 >= P.max_iter) || ld_volatile_i32(status) != DEV_OK;
                 sh->s_dec = stop;
                 if (stop && b == 0) {
                     P.st->iters = s - 1;
                     P.st->err = ed;
-                    P.st->converged = (ed <= P.tol);
+                    P.st->converged = (ed <= stop_tol(P.tol));
                     P.st->exit_reason = 0;
                 }
             }
@@ -550,10 +555,10 @@ ot_status lowp_solve_t(ot_assoc_ctx* ctx, const SolveArgs& a, double absorb_log2
     StreamCfg S;
     size_t smem = 0;
     int V = 1;
-    if (!plan_stage(nteams, I, Jp, ldk, 1, 24576, (size_t)1 << 40, &S, &smem, &V, (int)sizeof(T)))
+    if (!plan_stage(nteams, I, Jp, ldk, 1, 24576, (size_t)1 << 40, &S, &smem, &V, (int)sizeof(T), 1))
         return set_error(ctx, OT_EUNSUPPORTED, "stored-kernel geometry");
     const int grid = std::max(1, std::min(V, ctx->num_sms));
-    if (!plan_stage(nteams, I, Jp, ldk, grid, 24576, 232448 - 4096, &S, &smem, &V, (int)sizeof(T)))
+    if (!plan_stage(nteams, I, Jp, ldk, grid, 24576, 232448 - 4096, &S, &smem, &V, (int)sizeof(T), 1))
         return set_error(ctx, OT_EUNSUPPORTED, "stored kernel does not fit the shared memory (I=%lld J=%d)",
                          (long long)I, J);
     if (allow_max_dynamic_smem(kk.fn, smem) != cudaSuccess) {
@@ -620,9 +625,14 @@ ot_status lowp_solve_t(ot_assoc_ctx* ctx, const SolveArgs& a, double absorb_log2
     int iters = 1, converged = 0, absorptions = 0;
     double err = 0.0;
     const int bgrid = (int)std::max<int64_t>(1, std::min<int64_t>((I + 7) / 8, 8LL * ctx->num_sms));
+    const size_t build_smem = 2 * sizeof(float) * (size_t)Jp;  // G pairs
+    if (build_smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(lp_build<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "lp_build attribute");
+    }
     for (int launch = 0;; ++launch) {
         if (iters >= a.max_iter) break;  // the first iteration's plan is the answer
-        lp_build<T><<<bgrid, 256, sizeof(float) * Jp, s>>>(a.C, a.ld, K, ldk, I, J, Jp, Fm, Gm, Fref, Gref, k_hi,
+        lp_build<T><<<bgrid, 256, build_smem, s>>>(a.C, a.ld, K, ldk, I, J, Jp, Fm, Gm, Fref, Gref, k_hi,
                                                            k_lo);
         cudaError_t e = cudaMemsetAsync(lst, 0, sizeof(LpState), s);
         if (e != cudaSuccess) return cuda_error(ctx, e, "memset");

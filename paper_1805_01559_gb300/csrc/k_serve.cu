@@ -96,7 +96,7 @@ __device__ __forceinline__ void sv_rebuild_rows(const SvPrep& Q, float* C, int64
     const float inv_ln2 = 1.4426950408889634f;
     const float l2_10 = 3.3219280948873622f;  // log2(10)
     const float a0 = -30.0f * 0.1f * l2_10;   // -PL0/10 log2(10), PL0 = 30 dB
-    const float half_n = 0.5f * 3.5f;         // log2 G = a0 + X/10 log2(10) - (n/2) log2 d^2
+    const float half_n = 0.5f * 3.5f;         // log2 G = a0 - X/10 log2(10) - (n/2) log2 d^2
     const float side = (float)Q.side, dt = (float)Q.dt;
     int bad = 0;
     for (int64_t i = r0 + warp; i < r1; i += nw) {
@@ -121,7 +121,8 @@ __device__ __forceinline__ void sv_rebuild_rows(const SvPrep& Q, float* C, int64
             } else {
                 const float dx = x - Q.rrh_xy[2 * j], dy = y - Q.rrh_xy[2 * j + 1];
                 const float d2 = fmaxf(fmaf(dx, dx, dy * dy), 100.0f);  // d >= 10 m
-                const float e = fmaf(Q.shadow[i * (int64_t)J + j], 0.1f * l2_10, a0) - half_n * __log2f(d2);
+                // shadowing X (dB) adds to the path loss: G = 10^(-(PL0 + 10 n log10 d + X) / 10)
+                const float e = fmaf(Q.shadow[i * (int64_t)J + j], -0.1f * l2_10, a0) - half_n * __log2f(d2);
                 v = Q.P[j] * ex2(e);
             }
             row[j] = v;
@@ -481,6 +482,66 @@ using namespace ota;
 
 extern "C" {
 
+ot_status ot_assoc_build_cost_mobile(ot_assoc_ctx* ctx, double* dev_xy, double* dev_v, const float* rrh_xy,
+                                     const float* shadow_db, const float* P, int64_t I, int64_t J, double dt,
+                                     double side_m, double N0, double W_hz, double mu, float* C_out, int64_t ld_c,
+                                     double eps_rel, double* eps_out, void* stream) {
+    using namespace ota;
+    if (!ctx) return OT_EINVAL;
+    if (!dev_xy || !dev_v || !rrh_xy || !shadow_db || !P || !C_out) return set_error(ctx, OT_EINVAL, "null pointer");
+    if (I <= 0 || J <= 0) return set_error(ctx, OT_EINVAL, "I and J must be positive");
+    if (J > (1 << 20)) return set_error(ctx, OT_EUNSUPPORTED, "J too large");
+    if (ld_c == 0) ld_c = J;
+    if (ld_c < J) return set_error(ctx, OT_EINVAL, "leading dimension < J");
+    if (!(dt >= 0.0) || !std::isfinite(dt) || !(side_m > 0.0) || !std::isfinite(side_m))
+        return set_error(ctx, OT_EINVAL, "need dt >= 0 and side_m > 0");
+    if (!(N0 >= 0.0) || !(W_hz > 0.0)) return set_error(ctx, OT_EINVAL, "need N0 >= 0 and W_hz > 0");
+    if (!(mu > 0.0) || !std::isfinite(mu)) return set_error(ctx, OT_EINVAL, "mu must be finite and > 0");
+    if (eps_out && !(eps_rel > 0.0)) return set_error(ctx, OT_EINVAL, "eps_rel must be > 0");
+    DeviceGuardLite g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    SvPrep pr;
+    std::memset(&pr, 0, sizeof(pr));
+    pr.dev_xy = dev_xy;
+    pr.dev_v = dev_v;
+    pr.rrh_xy = rrh_xy;
+    pr.shadow = shadow_db;
+    pr.P = P;
+    pr.dt = dt;
+    pr.side = side_m;
+    pr.N0 = (float)N0;
+    pr.W = (float)W_hz;
+    pr.mu = (float)mu;
+    ot_status st = OT_OK;
+    char* state = (char*)scratch(ctx, SLOT_MISC, 256, &st);
+    if (st) return st;
+    int* dstat = (int*)state;
+    double* dmed = (double*)(state + 64);
+    cudaError_t e = cudaMemsetAsync(dstat, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "memset");
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((I + 63) / 64, 4LL * ctx->num_sms));
+    sv_rebuild_all<<<grid, 256, 0, s>>>(pr, C_out, ld_c, I, (int)J, dstat);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "mobile cost");
+    ctx->launches += 1;
+    if (!eps_out) return OT_OK;
+    st = launch_median(ctx, C_out, I, J, ld_c, dmed, s);
+    if (st) return st;
+    struct {
+        int bad;
+        int pad;
+        double med;
+    }* h = (decltype(h))host_staging(ctx, 64, &st);
+    if (st) return st;
+    e = cudaMemcpyAsync(&h->bad, dstat, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h->med, dmed, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "mobile cost");
+    if (h->bad != DEV_OK) return set_error(ctx, OT_EINVAL, "some rate is not finite and > 0");
+    *eps_out = eps_rel * h->med;
+    return OT_OK;
+}
+
 ot_status ot_assoc_server_create(ot_assoc_ctx* ctx, const ot_assoc_server_config* cfg, ot_assoc_server** out) {
     if (!ctx) return OT_EINVAL;
     if (!out) return set_error(ctx, OT_EINVAL, "null output pointer");
@@ -505,7 +566,7 @@ ot_status ot_assoc_server_create(ot_assoc_ctx* ctx, const ot_assoc_server_config
     // device memory: control, result slots, group state
     auto al = [](size_t x) { return (size_t)round_up((int64_t)x, 256); };
     const size_t Jp = (size_t)round_up(maxJ, 4), nv = VMAX;
-    const size_t gbytes = 1024 + al(3 * Jp * 8) + al(nv * 2 * Jp * 4) + al(nv * 16) + al(nv * Jp * 16) +
+    const size_t gbytes = 1024 + al(gstate_bytes((int)Jp)) + al(nv * 2 * Jp * 4) + al(nv * 16) + al(nv * Jp * 16) +
                           al((size_t)s->gsize * BT_NW * 16 + nv * 8);
     const size_t o_ctl = 0, o_res = al(sizeof(SvCtl)), o_gbar = o_res + al(sizeof(BRes) * SV_CAP);
     const size_t o_gcur = o_gbar + al(sizeof(unsigned) * s->ngroups), o_groups = o_gcur + al(sizeof(int) * s->ngroups);
@@ -532,7 +593,7 @@ ot_status ot_assoc_server_create(ot_assoc_ctx* ctx, const ot_assoc_server_config
         G.ls = (LoopState*)(p + 512);
         size_t o = 1024;
         G.G = (double*)(p + o);
-        o += al(3 * Jp * 8);
+        o += al(gstate_bytes((int)Jp));
         G.colpart = (float*)(p + o);
         o += al(nv * 2 * Jp * 4);
         G.errpart = (double*)(p + o);

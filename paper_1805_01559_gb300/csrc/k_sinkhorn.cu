@@ -335,7 +335,7 @@ struct SolveBufs {
     LoopState* ls;
     SolveSummary* summ;
     double2* cols;    // [Jp]
-    double* G;        // [3][Jp]
+    double* G;        // gstate_words(Jp)
     double* errpart;  // [2][nb]: loop residual pairs, then the finalize row residuals
     void* colpart;    // [nb][Jp] float2
     double2* fpart;   // [nb][Jp]
@@ -434,7 +434,7 @@ ot_status solve_bufs(ot_assoc_ctx* ctx, const LoopLaunch& LL, int Jp, SolveBufs*
     if (st) return st;
     B->fpart = (double2*)scratch(ctx, SLOT_FINPART, sizeof(double2) * (size_t)LL.V * Jp, &st);
     if (st) return st;
-    B->G = (double*)scratch(ctx, SLOT_G, sizeof(double) * 3 * (size_t)Jp, &st);
+    B->G = (double*)scratch(ctx, SLOT_G, gstate_bytes(Jp), &st);
     if (st) return st;
     B->errpart = (double*)scratch(ctx, SLOT_ERRPART, sizeof(double) * 2 * (size_t)LL.V, &st);
     if (st) return st;
@@ -733,31 +733,25 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 // Byte offsets inside g_noalloc_scratch (all multiples of 256).
 static constexpr size_t NA_STATE = 0;                                     // DevScalars/LoopState/summary
 static constexpr size_t NA_COLS = 4096;                                   // Jp double2
-static constexpr size_t NA_G = NA_COLS + 16 * NOALLOC_MAX_J;              // 3 * Jp doubles
-static constexpr size_t NA_ERRPART = NA_G + 24 * NOALLOC_MAX_J;           // 2 * CTAs doubles
+static constexpr size_t NA_G = NA_COLS + 16 * NOALLOC_MAX_J;              // gstate_words(Jp) doubles
+static constexpr size_t NA_ERRPART = NA_G + (gstate_bytes(NOALLOC_MAX_J) + 255) / 256 * 256;  // 2 * CTAs doubles
 static constexpr size_t NA_COLPART = NA_ERRPART + 16 * NOALLOC_MAX_CTAS;  // CTAs * Jp float2
 static constexpr size_t NA_FPART = NA_COLPART + 8 * (size_t)NOALLOC_MAX_CTAS * NOALLOC_MAX_J;  // CTAs * Jp double2
 static constexpr size_t NA_END = NA_FPART + 16 * (size_t)NOALLOC_MAX_CTAS * NOALLOC_MAX_J;
 static_assert(NA_END <= NOALLOC_BYTES, "no-allocation scratch layout does not fit");
 static_assert(NA_COLPART % 256 == 0 && NA_FPART % 256 == 0, "alignment");
 
-// Device address of g_noalloc_scratch per device, looked up once with that device current.
-static std::mutex g_noalloc_mu;
-static unsigned char* g_noalloc_ptr[128];
-
-static ot_status noalloc_base(int dev, unsigned char** out) {
-    if (dev < 0 || dev >= 128) return OT_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return OT_ECUDA;
-        }
-        g_noalloc_ptr[dev] = (unsigned char*)p;
+// Device address of g_noalloc_scratch in the current device's context, looked up on every
+// call.  The lookup allocates nothing and is cheap; caching it would keep a dead address once
+// the context that loaded the module is destroyed and re-created (cudaDeviceReset).
+static ot_status noalloc_base(unsigned char** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return OT_ECUDA;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = (unsigned char*)p;
     return OT_OK;
 }
 
@@ -772,7 +766,7 @@ static ot_status noalloc_solve(const SolveArgs& a, SolveSummary* sum_host) {
         return OT_ECUDA;
     }
     unsigned char* base = nullptr;
-    ot_status st = noalloc_base(dev, &base);
+    ot_status st = noalloc_base(&base);
     if (st) return st;
     Kernels kk;
     if (!pick_kernels(J, &kk)) return OT_EUNSUPPORTED;

@@ -23,6 +23,12 @@ struct DevScalars {
     int status;
 };
 
+// The loop test compares the FP32 residual of the plan with tol (1 - 2^-5).  That residual is
+// formed from FP32 cell values (approximate ex2, one rounding at about |G| per exponent) and
+// sits within about 1e-8 of the exact FP64 residual of the same potentials at tol = 1e-6 (it
+// can be on either side); the 3% margin keeps the returned plan's exact residual <= tol.
+__host__ __device__ __forceinline__ double stop_tol(double tol) { return tol * (1.0 - 0.03125); }
+
 struct LoopState {
     unsigned bar;
     int status;
@@ -30,6 +36,25 @@ struct LoopState {
     int converged;
     double err;
 };
+
+// Column state of one solve in global memory (Jp a multiple of 4), in doubles:
+//   [0, 2 Jp)       G^k (log2 units, FP64) in buffer k & 1 (the returned potentials)
+//   [2 Jp, 3 Jp)    log2 q^_j (FP64)
+//   [3 Jp, 4 Jp)    log2 q^_j as FP32 pairs
+//   [4 Jp, 4.5 Jp)  fixed-point shift S_j of column j (int)
+//   then 3 rows of Jp + 4 64-bit words: per-column fixed-point totals of a sweep's column
+//   partials and its row residual (word Jp); sweep s adds into row s mod 3.
+// The totals are sums of integers, the same in any order, so every CTA reads the same column
+// sums whatever the number of CTAs or the order in which partitions arrive.
+static constexpr int FX_BITS = 40;   // a column total of q^_j is about 2^40 units
+static constexpr int FX_ERR = 50;    // row residuals in units of 2^-50
+__host__ __device__ constexpr size_t gstate_words(int Jp) { return (size_t)Jp * 15 / 2 + 12; }
+__host__ __device__ constexpr size_t gstate_bytes(int Jp) { return 8 * gstate_words(Jp); }
+__device__ __forceinline__ float2* gs_lq2(double* G, int Jp) { return reinterpret_cast<float2*>(G + 3 * (size_t)Jp); }
+__device__ __forceinline__ int* gs_sx(double* G, int Jp) { return reinterpret_cast<int*>(G + 4 * (size_t)Jp); }
+__device__ __forceinline__ unsigned long long* gs_acc(double* G, int Jp) {
+    return reinterpret_cast<unsigned long long*>(G + 4 * (size_t)Jp + Jp / 2);
+}
 
 template <int TW, int VPT>
 __device__ __forceinline__ void load_G(const double* __restrict__ G, int J, int tl, float4 (&g)[VPT]) {
@@ -48,6 +73,15 @@ __device__ __forceinline__ void load_G(const double* __restrict__ G, int J, int 
 // gives -inf and never inf - inf.
 __device__ __forceinline__ float expo(float F_hi, float F_lo_plus_G, float c, float k_hi, float k_lo) {
     return fmaf(-c, k_hi, F_hi) + fmaf(-c, k_lo, F_lo_plus_G);
+}
+
+// The same with the column potential as an FP32 pair G = G_hi + G_lo: F_hi - C k_hi (one
+// rounding at about |G|) meets G_hi first, where the two nearly cancel on the cells that
+// carry mass, and the low parts join at the magnitude of |x|.  No rounding of G itself enters
+// the plan, so the plan the sweep measures is the plan of the FP64 potentials it returns.
+__device__ __forceinline__ float expo2(float F_hi, float F_lo_plus_G_lo, float G_hi, float c, float k_hi,
+                                       float k_lo) {
+    return (fmaf(-c, k_hi, F_hi) + G_hi) + fmaf(-c, k_lo, F_lo_plus_G_lo);
 }
 
 // Error-free sum a + b = s + e (Knuth's two-sum).
@@ -105,10 +139,16 @@ struct StreamCfg {
     int off_ring;
 };
 
-// Column potentials as FP32 in shared memory (padding columns 0).
+// Column potentials as FP32 pairs in shared memory: high parts Gs[0, Jp), low parts
+// Gs[Jp, 2 Jp) with G_j = hi + lo to about 2^-48 relative (padding columns 0).
 __device__ __forceinline__ void load_G_smem(const double* __restrict__ G, int J, int Jp, float* Gs, int tid,
                                             int nthreads) {
-    for (int j = tid; j < Jp; j += nthreads) Gs[j] = (j < J) ? (float)G[j] : 0.0f;
+    for (int j = tid; j < Jp; j += nthreads) {
+        const double x = (j < J) ? G[j] : 0.0;
+        const float hi = (float)x;
+        Gs[j] = hi;
+        Gs[Jp + j] = (float)(x - (double)hi);
+    }
 }
 
 // log2(r) for the row and column corrections: a short series when r is within 2^-7 of 1
@@ -236,8 +276,8 @@ struct SolveParams {
     const unsigned long long* input_bad;  // nonzero => invalid rates upstream, or nullptr
     DevScalars* sc;
     LoopState* st;
-    double* G;        // [3][Jp]: column potentials G^k (log2 units, FP64) in buffer k & 1,
-                      // then log2 q^_j (set once per solve)
+    double* G;        // gstate_words(Jp): column potentials G^k (log2 units, FP64) in buffer
+                      // k & 1, log2 q^_j, the fixed-point column totals (see gstate_words)
     float2* F_out;    // [I] row potentials of the returned plan (hi, lo), or nullptr
     float* colpart;   // [V][2 * Jp]
     double* errpart;  // [V] during setup (sums of p); reused as float2 [V] residual pairs
@@ -299,12 +339,12 @@ __host__ __device__ __forceinline__ int parts_for(int64_t I, int rs) {
 }
 
 // Stage geometry and shared-memory layout of an instance solved by nb CTAs with teams of
-// `nteams` rows.  The rows per stage depend only on the stage target and the row length,
+// `nteams` rows (g_words floats per column at off_G: 2 for the FP32 pairs of G).  The rows per stage depend only on the stage target and the row length,
 // and the partitions only on I and the rows per stage: the arithmetic of a solve is fixed
 // by (I, J, ld, stage target) whatever nb is.  Returns false when a CTA's rows do not fit
 // next to two stages.
 inline bool plan_stage(int nteams, int64_t I, int Jp, int64_t ld, int nb, int stage_target, size_t budget,
-                       StreamCfg* S, size_t* smem, int* Vout, int esize = 4) {
+                       StreamCfg* S, size_t* smem, int* Vout, int esize = 4, int g_words = 2) {
     const size_t comb = (size_t)((nteams + 1) / 2) * Jp * sizeof(float);
     const size_t row_bytes = (size_t)ld * esize;
     const int rpt = (int)(stage_target / ((size_t)nteams * row_bytes) > 1 ? stage_target / ((size_t)nteams * row_bytes)
@@ -319,7 +359,7 @@ inline bool plan_stage(int nteams, int64_t I, int Jp, int64_t ld, int nb, int st
     }
     auto up = [](size_t x, size_t m) { return (x + m - 1) / m * m; };
     const size_t off_G = up(SMEM_HDR + comb, 16);
-    const size_t off_F = up(off_G + (size_t)Jp * sizeof(float), 16);
+    const size_t off_F = up(off_G + (size_t)g_words * Jp * sizeof(float), 16);  // G pairs: hi, then lo
     const size_t off_P = off_F + (size_t)2 * rmax * sizeof(float2);
     const size_t off_ring = up(off_P + (size_t)rmax * sizeof(float), 128);
     const size_t stage = (size_t)rs * row_bytes;
@@ -498,10 +538,11 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
                 if (chunk_inside<TW, VPT>(v) || col < J) {
                     float4 x = EUC ? euclid_chunk(dxy, rx, rx + Jp, col, J) : *reinterpret_cast<const float4*>(row + col);
                     float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+                    float4 gl = *reinterpret_cast<const float4*>(Gs + Jp + col);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const float cost = comp(x, c);
-                        float t = ex2(expo(F.x, F.y + comp(gv, c), cost, P.k_hi, P.k_lo));
+                        float t = ex2(expo2(F.x, F.y + comp(gl, c), comp(gv, c), cost, P.k_hi, P.k_lo));
                         if (!chunk_inside<TW, VPT>(v) && col + c >= J) t = 0.f;  // past the row
                         rsum += t;
                         comp(cpi[v], c) = fmaf(phat, t, comp(cpi[v], c));
@@ -567,7 +608,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
     uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
     uint64_t* empty = full + MAX_STAGES;
     float* comb = reinterpret_cast<float*>(dyn + SMEM_HDR);    // [ceil(NTEAMS / 2)][Jp]
-    float* Gs = reinterpret_cast<float*>(dyn + S.off_G);       // [Jp]
+    float* Gs = reinterpret_cast<float*>(dyn + S.off_G);       // [2][Jp]: G pairs (hi, lo)
     float2* Fs = reinterpret_cast<float2*>(dyn + S.off_F);     // [2][rmax]
     float* Ps = reinterpret_cast<float*>(dyn + S.off_P);       // [rmax]
     float* ring = reinterpret_cast<float*>(dyn + S.off_ring);  // [stages][stage_floats]
@@ -575,7 +616,6 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
     float* red = sh->red;
     float* errf = sh->errf;
     double(*sh_sum)[2] = sh->sh_sum;
-    int& s_dec = sh->s_dec;
     int& s_bad = sh->s_bad;
     volatile int& s_stop = sh->s_stop;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -684,9 +724,22 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
     }
     const double inv_sq = 1.0 / sq;
     double* LQ = P.G + 2 * Jp;  // log2 q^_j, formed once here (read after the next grid barrier)
+    float2* LQ2 = gs_lq2(P.G, Jp);
+    int* SX = gs_sx(P.G, Jp);
+    unsigned long long* ACC = gs_acc(P.G, Jp);
     {
         const int gw = b * NCW + warp, nw = nb * NCW;
-        for (int j = gw * 32 + lane; j < J; j += nw * 32) LQ[j] = log2((double)__ldcg(P.q + j) * inv_sq);
+        for (int j = gw * 32 + lane; j < J; j += nw * 32) {
+            const double lq = log2((double)__ldcg(P.q + j) * inv_sq);
+            LQ[j] = lq;
+            const float hi = (float)lq;
+            LQ2[j] = make_float2(hi, (float)(lq - (double)hi));
+            // the total of column j is about 2^FX_BITS when its sum is q^_j; shifts that the
+            // FP32 scale cannot carry send the column to the exact path (shift 0 = "never")
+            const int sx = FX_BITS - (int)floor(lq);
+            SX[j] = sx <= 126 ? sx : 0;
+        }
+        for (int t = (b * NCW + warp) * 32 + lane; t < 3 * (Jp + 4); t += nw * 32) ACC[t] = 0ull;
         const float inv_sp_f = (float)(1.0 / sp);
         for (int r = tid; r < nrow; r += NC) Ps[r] *= inv_sp_f;  // p^_i
         bar_named(CONS_BAR, NC);
@@ -750,9 +803,10 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                 for (int v = 0; v < VPT; ++v) {
                     const int col = 4 * (tm.tl + TT * v);
                     float4 gv = col < Jp ? *reinterpret_cast<const float4*>(Gs + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 gl = col < Jp ? *reinterpret_cast<const float4*>(Gs + Jp + col) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const float z = expo(-m, comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo);
+                        const float z = expo2(-m, comp(gl, c), comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo);
                         comp(x[v], c) = z;
                         s += ex2(z);
                     }
@@ -878,8 +932,7 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                     if (!(ss > 0.0) || !isfinite(ss)) {
                         atomicCAS(status, DEV_OK, DEV_ENUMERIC);
                     } else {
-                        const double Gu = (double)(float)P.G[j];
-                        P.G[Jp + j] = Gu + LQ[j] - ((double)mm + log2(ss));
+                        P.G[Jp + j] = P.G[j] + LQ[j] - ((double)mm + log2(ss));
                     }
                 }
             }
@@ -890,8 +943,11 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
     }
 
     // ---- sweeps 2, 3, ...: one read of C and one ex2 per cell -----------------------------
-    float2* errp = reinterpret_cast<float2*>(P.errpart);
+    // Each partition adds its column partials (and row residual) as fixed-point integers into
+    // the row of totals of this sweep; after the one grid barrier of the iteration every CTA
+    // reads the totals and forms all column updates itself in its shared-memory copy of G.
     for (int s = 2;; ++s) {
+        unsigned long long* acc_s = ACC + (size_t)(s % 3) * (Jp + 4);
         const float2* Fold = Fs + ((s - 1) & 1) * S.rmax;  // F'^(s-1)
         float2* Fnew = Fs + (s & 1) * S.rmax;
         float4 acc[VPT];
@@ -924,9 +980,10 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                     const int col = 4 * (tm.tl + TT * v);
                     if (chunk_inside<TW, VPT>(v) || col < J) {  // chunks past the row carry no mass
                         float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+                        float4 gl = *reinterpret_cast<const float4*>(Gs + Jp + col);
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
-                            const float t = ex2(expo(F.x, F.y + comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
+                            const float t = ex2(expo2(F.x, F.y + comp(gl, c), comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
                             comp(x[v], c) = t;
                             rsum += t;
                         }
@@ -953,14 +1010,23 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             if (!EUC && lane == 0) mbar_arrive(&empty[st]);
             ++cseq;
           }
-            // end of partition vp: its column partials (teams in order) and row residual
+            // end of partition vp: its column partials (teams in order) and row residual.  The
+            // FP32 partial is kept for the exact path and added to the column's total as
+            // round(partial 2^S_j); a partial too large for the total marks the column.
             if (tm.tl == 0) errf[tm.team] = errt;
             float* cp = P.colpart + (int64_t)vp * Jp;
-            cta_col_sum<TW, VPT>(comb, acc, J, Jp, tm, [&](int j, float sum) { cp[j] = sum; });
+            cta_col_sum<TW, VPT>(comb, acc, J, Jp, tm, [&](int j, float sum) {
+                cp[j] = sum;
+                const int sx = SX[j];
+                const float x = ldexpf(sum, sx);
+                if (sx != 0 && x < 0x1p55f) atomicAdd(acc_s + j, (unsigned long long)__float2ull_rn(x));
+                else atomicOr(acc_s + j, 1ull << 63);
+            });
             if (tid == 0) {
                 float2 e = make_float2(errf[0], 0.f);
                 for (int t = 1; t < NTEAMS; ++t) e = df_add(e, errf[t]);
-                errp[vp] = e;
+                atomicAdd(acc_s + Jp, (unsigned long long)__float2ull_rn(ldexpf(e.x + e.y, FX_ERR)));
+                s_bad = 0;
             }
 #pragma unroll
             for (int v = 0; v < VPT; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -968,45 +1034,15 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             if (vp + 1 < v1) bar_named(CONS_BAR, NC);  // errf is read by thread 0 above
         }
         OTA_BARRIER();
-        // Loop test on pi^(s-1) (warp 0; every CTA forms the same total in the same order)
-        // while the other warps already form G^s into the other buffer: G^(s-1) stays intact
-        // for a stop.  All sums here are FP32 pairs: no FP64 in the per-sweep path.
-        if (warp == 0) {
-            float2 e = make_float2(0.f, 0.f);
-            for (int bb = lane; bb < V; bb += 32) e = df_add2(e, errp[bb]);
-            e = warp_sum_df(e);
-            if (lane == 0) {
-                const double ed = (double)e.x + (double)e.y;
-                const int stop = (ed <= P.tol) || (s - 1 >= P.max_iter);
-                s_dec = stop;
-                if (stop && b == 0) {
-                    P.st->iters = s - 1;
-                    P.st->err = ed;
-                    P.st->converged = (ed <= P.tol);
-                }
+        // Loop test on pi^(s-1): every thread reads the same total of the row residuals.
+        const double ed = (double)__ldcg(acc_s + Jp) * 0x1p-50;
+        const bool conv = ed <= stop_tol(P.tol);
+        if (conv || s - 1 >= P.max_iter) {
+            if (b == 0 && tid == 0) {
+                P.st->iters = s - 1;
+                P.st->err = ed;
+                P.st->converged = conv;
             }
-        }
-        {
-            const double* Gold = P.G + ((s - 1) & 1) * Jp;
-            double* Gnew = P.G + (s & 1) * Jp;
-            const int gw = b * (NCW - 1) + (warp - 1), nw = nb * (NCW - 1);
-            for (int j = gw; warp > 0 && j < J; j += nw) {
-                float2 sum = make_float2(0.f, 0.f);
-                for (int bb = lane; bb < V; bb += 32) sum = df_add(sum, P.colpart[(int64_t)bb * Jp + j]);
-                sum = warp_sum_df(sum);
-                if (lane == 0) {
-                    if (!(sum.x > 0.f) || !isfinite(sum.x)) {
-                        atomicCAS(status, DEV_OK, DEV_ENUMERIC);
-                    } else {
-                        const float2 ls = df_log2(sum);  // log2 s_j = ls.x + ls.y
-                        const float Gu = (float)Gold[j];
-                        Gnew[j] = ((double)Gu - (double)ls.x) + (LQ[j] - (double)ls.y);
-                    }
-                }
-            }
-        }
-        bar_named(CONS_BAR, NC);
-        if (s_dec) {
             if (P.F_out)
                 for (int r = tid; r < nrow; r += NC) P.F_out[r0 + r] = Fold[r];
             *ret_par = (s - 1) & 1;
@@ -1014,9 +1050,64 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             if (tid == 0) s_stop = 1;
             return true;
         }
-        OTA_BARRIER_CHECK();
-        load_G_smem(P.G + (s & 1) * Jp, J, Jp, Gs, tid, NC);
-        bar_named(CONS_BAR, NC);
+        // G^s_j = G^(s-1)_j + log2 q^_j - log2 s_j, every column in every CTA (FP32 pairs).  The
+        // sum s_j is the fixed-point total T_j 2^-S_j; a marked column, or one whose total is
+        // too small to carry 30 bits, is summed exactly from the partitions' FP32 partials.
+        {
+            double* Gnew = P.G + (s & 1) * Jp;
+            int bad = 0;
+            // CU columns a thread per round: all loads of a round first (one trip to L2), then
+            // the arithmetic
+            constexpr int CU = 3;
+            for (int j0 = tid; j0 < J; j0 += CU * NC) {
+                unsigned long long T[CU];
+                float2 lq[CU];
+                int sx[CU];
+#pragma unroll
+                for (int u = 0; u < CU; ++u) {
+                    const int j = j0 + u * NC;
+                    T[u] = j < J ? __ldcg(acc_s + j) : 0ull;
+                    lq[u] = j < J ? __ldcg(LQ2 + j) : make_float2(0.f, 0.f);
+                    sx[u] = j < J ? __ldcg(SX + j) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < CU; ++u) {
+                    const int j = j0 + u * NC;
+                    if (j >= J) break;
+                    float2 ls;
+                    if (!(T[u] >> 63) && T[u] >= (1ull << 30)) {
+                        const float th = __ull2float_rn(T[u]);
+                        const float tl = (float)((long long)T[u] - (long long)__float2ull_rn(th));
+                        ls = df_log2(make_float2(th, tl));
+                        ls.x -= (float)sx[u];
+                    } else {
+                        float2 sum = make_float2(0.f, 0.f);
+                        for (int v = 0; v < V; ++v) sum = df_add(sum, __ldcg(P.colpart + (int64_t)v * Jp + j));
+                        if (!(sum.x > 0.f) || !isfinite(sum.x)) {
+                            bad = 1;
+                            continue;
+                        }
+                        ls = df_log2(sum);
+                    }
+                    const float2 d = df_add2(lq[u], make_float2(-ls.x, -ls.y));
+                    const float2 Gn = df_add2(make_float2(Gs[j], Gs[Jp + j]), d);
+                    Gs[j] = Gn.x;
+                    Gs[Jp + j] = Gn.y;
+                    if ((j >> 5) % nb == b) Gnew[j] = (double)Gn.x + (double)Gn.y;  // the FP64 copy, once
+                }
+            }
+            // this CTA's share of clearing the totals of sweep s + 2 (last read before this
+            // iteration's barrier; next written after the next one)
+            unsigned long long* acc_z = ACC + (size_t)((s + 2) % 3) * (Jp + 4);
+            for (int t = b * NC + tid; t < Jp + 4; t += nb * NC) acc_z[t] = 0ull;
+            if (bad) atomicOr(&s_bad, 1);
+            bar_named(CONS_BAR, NC);
+            if (s_bad) {  // every CTA sees the same totals and takes the same decision
+                if (tid == 0) atomicCAS(status, DEV_OK, DEV_ENUMERIC);
+                if (tid == 0) s_stop = 1;
+                return false;
+            }
+        }
     }
 #undef OTA_BARRIER_CHECK
 #undef OTA_BARRIER

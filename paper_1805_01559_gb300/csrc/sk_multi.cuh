@@ -29,7 +29,8 @@ struct MultiParams {
 };
 
 // Shared-memory layout: StreamCfg offsets with the column potentials of solve s at
-// off_G + 4 Jp s and its row potential buffers at off_F + 16 rmax s.
+// off_G + 8 Jp s (FP32 pairs: Jp high parts, then Jp low parts) and its row potential
+// buffers at off_F + 16 rmax s.
 inline bool plan_multi(int nteams, int n, int64_t I, int Jp, int64_t ld, int nb, int stage_target, size_t budget,
                        StreamCfg* S, size_t* smem, int* Vout) {
     const size_t comb = (size_t)((nteams + 1) / 2) * Jp * sizeof(float);
@@ -47,7 +48,7 @@ inline bool plan_multi(int nteams, int n, int64_t I, int Jp, int64_t ld, int nb,
     if (rmax < 1) rmax = 1;
     auto up = [](size_t x, size_t m) { return (x + m - 1) / m * m; };
     const size_t off_G = up(SMEM_HDR + comb, 16);
-    const size_t off_F = up(off_G + (size_t)n * Jp * sizeof(float), 16);
+    const size_t off_F = up(off_G + (size_t)2 * n * Jp * sizeof(float), 16);
     const size_t off_P = off_F + (size_t)n * 2 * rmax * sizeof(float2);
     const size_t off_ring = up(off_P + (size_t)rmax * sizeof(float), 128);
     const size_t stage = (size_t)rs * row_bytes;
@@ -125,9 +126,10 @@ __device__ __forceinline__ bool ms_first_sweep(const SolveParams& P, const Strea
                 for (int v = 0; v < VPT; ++v) {
                     const int col = 4 * (tm.tl + TT * v);
                     float4 gv = col < Jp ? *reinterpret_cast<const float4*>(Gs + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 gl = col < Jp ? *reinterpret_cast<const float4*>(Gs + Jp + col) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const float z = expo(-m, comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo);
+                        const float z = expo2(-m, comp(gl, c), comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo);
                         comp(x[v], c) = z;
                         s += ex2(z);
                     }
@@ -247,8 +249,7 @@ __device__ __forceinline__ bool ms_first_sweep(const SolveParams& P, const Strea
                 if (!(ss > 0.0) || !isfinite(ss)) {
                     atomicCAS(g.status, DEV_OK, DEV_ENUMERIC);
                 } else {
-                    const double Gu = (double)(float)P.G[j];
-                    P.G[Jp + j] = Gu + LQ[j] - ((double)mm + log2(ss));
+                    P.G[Jp + j] = P.G[j] + LQ[j] - ((double)mm + log2(ss));
                 }
             }
         }
@@ -388,7 +389,7 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
         }
         const float inv_sp_f = (float)(1.0 / sp);
         for (int r = tid; r < nrow; r += NC) Ps[r] *= inv_sp_f;
-        for (int s = 0; s < n; ++s) load_G_smem(M.P[s].G, J, Jp, Gbase + (size_t)s * Jp, tid, NC);
+        for (int s = 0; s < n; ++s) load_G_smem(M.P[s].G, J, Jp, Gbase + (size_t)2 * s * Jp, tid, NC);
         bar_named(CONS_BAR, NC);
     }
     // LQ of solve s is read after the first grid barrier of its first iteration
@@ -398,7 +399,7 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
 
     // ---- the exact first iteration, one solve after the other ---------------------------
     for (int s = 0; s < n; ++s) {
-        if (!ms_first_sweep<TW, VPT>(M.P[s], S, g, sh, dyn, Gbase + (size_t)s * Jp,
+        if (!ms_first_sweep<TW, VPT>(M.P[s], S, g, sh, dyn, Gbase + (size_t)2 * s * Jp,
                                       Fbase + (size_t)s * 2 * S.rmax + S.rmax, Ps, nrow, v0, v1, cseq, par)) {
             if (tid == 0) s_stop = 1;
             return false;
@@ -443,7 +444,7 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
                             FF[s] = make_float2(0.f, 0.f);
                             if (!((active >> s) & 1u)) continue;
                             const SolveParams& P = M.P[s];
-                            const float* Gs = Gbase + (size_t)s * Jp;
+                            const float* Gs = Gbase + (size_t)2 * s * Jp;
                             const float2* Fold = Fbase + (size_t)s * 2 * S.rmax + ((it - 1) & 1) * S.rmax;
                             float2* Fnew = Fbase + (size_t)s * 2 * S.rmax + (it & 1) * S.rmax;
                             const float2 F = Fold[lr];
@@ -454,9 +455,11 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
                                 const int col = 4 * (tm.tl + TT * v);
                                 if (chunk_inside<TW, VPT>(v) || col < J) {
                                     float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+                                    float4 gl = *reinterpret_cast<const float4*>(Gs + Jp + col);
 #pragma unroll
                                     for (int c = 0; c < 4; ++c)
-                                        rsum += ex2(expo(F.x, F.y + comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
+                                        rsum += ex2(expo2(F.x, F.y + comp(gl, c), comp(gv, c), comp(x[v], c), P.k_hi,
+                                                          P.k_lo));
                                 }
                             }
                             rsum = team_reduce<TW, float, false>(rsum, red, NTEAMS, tm, par);
@@ -469,7 +472,7 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
                         for (int s = 0; s < NS; ++s) {
                             if (!((active >> s) & 1u)) continue;
                             const SolveParams& P = M.P[s];
-                            const float* Gs = Gbase + (size_t)s * Jp;
+                            const float* Gs = Gbase + (size_t)2 * s * Jp;
                             const float2 F = FF[s];
                             const float d = dd[s];
 #pragma unroll
@@ -477,9 +480,11 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
                                 const int col = 4 * (tm.tl + TT * v);
                                 if (chunk_inside<TW, VPT>(v) || col < J) {
                                     float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+                                    float4 gl = *reinterpret_cast<const float4*>(Gs + Jp + col);
 #pragma unroll
                                     for (int c = 0; c < 4; ++c) {
-                                        const float t = ex2(expo(F.x, F.y + comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
+                                        const float t = ex2(expo2(F.x, F.y + comp(gl, c), comp(gv, c), comp(x[v], c),
+                                                                  P.k_hi, P.k_lo));
                                         comp(acc[s][v], c) = fmaf(t, d, comp(acc[s][v], c));
                                     }
                                 }
@@ -491,7 +496,7 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
                     for (int s = 0; s < NS; ++s) {
                         if (!((active >> s) & 1u)) continue;  // uniform over the launch
                         const SolveParams& P = M.P[s];
-                        const float* Gs = Gbase + (size_t)s * Jp;
+                        const float* Gs = Gbase + (size_t)2 * s * Jp;
                         const float2* Fold = Fbase + (size_t)s * 2 * S.rmax + ((it - 1) & 1) * S.rmax;
                         float2* Fnew = Fbase + (size_t)s * 2 * S.rmax + (it & 1) * S.rmax;
                         const float2 F = Fold[lr];
@@ -502,9 +507,11 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
                             const int col = 4 * (tm.tl + TT * v);
                             if (chunk_inside<TW, VPT>(v) || col < J) {
                                 float4 gv = *reinterpret_cast<const float4*>(Gs + col);
+                                float4 gl = *reinterpret_cast<const float4*>(Gs + Jp + col);
 #pragma unroll
                                 for (int c = 0; c < 4; ++c) {
-                                    const float t = ex2(expo(F.x, F.y + comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
+                                    const float t = ex2(expo2(F.x, F.y + comp(gl, c), comp(gv, c), comp(x[v], c), P.k_hi,
+                                                              P.k_lo));
                                     comp(t4[v], c) = t;
                                     rsum += t;
                                 }
@@ -561,13 +568,14 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
                 e = warp_sum_df(e);
                 if (lane == 0) {
                     const double ed = (double)e.x + (double)e.y;
-                    const int stop = (ed <= P.tol) || (it - 1 >= P.max_iter);
+                    const bool conv = ed <= stop_tol(P.tol);
+                    const int stop = conv || (it - 1 >= P.max_iter);
                     if (stop) {
                         atomicOr(&sh->s_dec, 1 << s);
                         if (b == 0) {
                             P.st->iters = it - 1;
                             P.st->err = ed;
-                            P.st->converged = (ed <= P.tol);
+                            P.st->converged = conv;
                         }
                     }
                 }
@@ -589,8 +597,7 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
                             atomicCAS(status, DEV_OK, DEV_ENUMERIC);
                         } else {
                             const float2 ls = df_log2(sum);
-                            const float Gu = (float)Gold[j];
-                            Gnew[j] = ((double)Gu - (double)ls.x) + (LQ[j] - (double)ls.y);
+                            Gnew[j] = (Gold[j] - (double)ls.x) + (LQ[j] - (double)ls.y);
                         }
                     }
                 }
@@ -610,7 +617,7 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
             return false;
         }
         for (int s = 0; s < n; ++s)
-            if ((active >> s) & 1u) load_G_smem(M.P[s].G + (it & 1) * Jp, J, Jp, Gbase + (size_t)s * Jp, tid, NC);
+            if ((active >> s) & 1u) load_G_smem(M.P[s].G + (it & 1) * Jp, J, Jp, Gbase + (size_t)2 * s * Jp, tid, NC);
         bar_named(CONS_BAR, NC);
     }
     if (ld_volatile_i32(status) != DEV_OK) {
@@ -620,7 +627,7 @@ __device__ __forceinline__ bool ms_consumers(const MultiParams& M, const StreamC
     // ---- finalize sweeps, one solve after the other ---------------------------------------
     for (int s = 0; s < n; ++s) {
         StreamCfg Ss = S;
-        Ss.off_G = S.off_G + (int)(sizeof(float) * (size_t)s * Jp);
+        Ss.off_G = S.off_G + (int)(sizeof(float) * (size_t)2 * s * Jp);
         const float2* Fold = Fbase + (size_t)s * 2 * S.rmax + retp[s] * S.rmax;
         sk_finalize_sweep<TW, VPT>(M.P[s], Ss, sh, dyn, r0, nrow, v0, v1, Fold, cseq, g.abort);
         bar_named(CONS_BAR, NC);

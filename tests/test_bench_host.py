@@ -89,3 +89,36 @@ def test_stored_euclid_instruction_count_follows_the_solver_sources(tmp_path, mo
     assert bench.stored_euclid_inst() is None
     monkeypatch.setattr(bench, "EUCLID_PROFILE", str(tmp_path / "missing.md"))
     assert bench.stored_euclid_inst() is None
+
+
+def test_solve_roofline_counts_iterations_of_every_launch():
+    # two steps of three solves: (kernel ms, iterations, completed sweeps)
+    per = [[(0.6, 17, 17), (0.8, 17, 17)], [(1.0, 27, 27), (1.0, 27, 27)], [(1.5, 41, 41), (1.5, 41, 41)]]
+    I, J, peak = 50_000, 800, 6000.0
+    r = bench.solve_roofline(per, I, J, peak)
+    cell = 4.0 * I * J
+    alg = cell * 2 * (17 + 27 + 41)
+    ms = 0.6 + 0.8 + 2 * 1.0 + 2 * 1.5
+    assert r["launches_timed"] == 6
+    assert r["achieved"] == pytest.approx(alg / 1e9 / (ms / 1e3))
+    assert r["alg_bytes_per_launch"] == pytest.approx(alg / 6)
+    assert r["frac_incl_setup_finalize"] == pytest.approx(cell * 2 * (19 + 29 + 43) / 1e9 / (ms / 1e3) / peak)
+    first = r["per_launch"][0]
+    assert first["iters"] == 17 and first["ms"] == pytest.approx(0.7)
+    assert first["frac"] == pytest.approx(cell * 17 / 1e9 / 0.7e-3 / peak)
+    assert bench.solve_roofline([[], [], []], I, J, peak)["achieved"] is None
+
+
+def test_clock_sampler_decodes_nvml_reason_bits():
+    cs = bench.ClockSampler(0)
+    cs._nvml = object()  # stands in for an opened NVML handle; nothing is polled
+
+    class _T:
+        def join(self, timeout=None):
+            pass
+
+    cs.t = _T()
+    cs.samples = [(2070.0, 2070.0, 0x0), (1900.0, 2070.0, 0x4), (2000.0, 2070.0, 0x4 | 0x40)]
+    out = cs.stop()
+    assert out["sm_mhz"] == 2000.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]

@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 RTOL_ITER = 2e-5
-MARG_SLACK = 5e-7
+MARG_SLACK = 0.0  # the device stops at FP32 residual <= tol (1 - 2^-5)
 
 
 @pytest.fixture(scope="module")

@@ -6,8 +6,15 @@ reported marginals and cost are evaluated exactly (FP64 reductions on the true C
 returned potentials, so they show the storage error:
   * FP32 storage: entries keep 24 bits; cost within 1e-5 of the oracle's converged cost;
   * BF16 storage: 8-bit mantissas (2^-9 relative per entry); FP16: 11 bits, entries below
-    2^-24 of a row flushed.  Target from the problem statement: cost within 1e-3 of the
-    FP64 oracle; marginal L1 of the returned potentials within 2e-3.
+    2^-24 of a row flushed.  Target from the problem statement: cost and the exact marginal
+    L1 of the returned potentials within 1e-3 of the FP64 oracle (measured at eps = 0.05
+    median(C): BF16 5e-4 on the 1000 x 50 instance, 1.7e-4 on the 20,000 x 512 subsample;
+    FP16 7e-5 and 2e-5).
+  * FP32 storage: the loop stops at residual <= tol (1 - 2^-5) like the log-domain solver,
+    so the exact marginal L1 stays <= tol.
+Absorption (the stabilised scaling form): a forced threshold of 0.25 (log2 units) rebuilds
+K~ every few iterations; FP16 at eps = 0.001 median(C) crosses the default threshold of 8 by
+itself.  Both are compared with the oracle at the same bounds.
 """
 import numpy as np
 import pytest
@@ -43,7 +50,7 @@ def _fmts():
 
 
 COST_TOL = {"f32": 1e-5, "bf16": 1e-3, "f16": 1e-3}
-MARG_TOL = {"f32": 2e-6, "bf16": 2e-3, "f16": 2e-3}
+MARG_TOL = {"f32": 1e-6, "bf16": 1e-3, "f16": 1e-3}
 
 
 def _case_c1():
@@ -78,8 +85,10 @@ def test_lowp_matches_oracle(ctx, fmt, case):
     assert abs(res.transport_cost - cost_or) <= COST_TOL[fmt] * cost_or, (res.transport_cost, cost_or)
     assert er <= MARG_TOL[fmt] and ec <= MARG_TOL[fmt], (er, ec)
     # the device summary evaluates the returned potentials on the true C (FP32 cells, FP64
-    # reductions): it agrees with the exact evaluation to FP32 cell accuracy
-    assert res.marg_err_row == pytest.approx(er, rel=1e-3, abs=1e-9)
+    # reductions): it agrees with the exact evaluation to FP32 cell accuracy, which leaves
+    # the residual within about 1e-8 absolute (approximate ex2 and one exponent rounding at
+    # about |G| per cell; measured 1-2e-9 at these sizes)
+    assert res.marg_err_row == pytest.approx(er, rel=1e-3, abs=1e-8)
     assert res.transport_cost == pytest.approx(cost, rel=1e-6)
 
 
@@ -99,6 +108,39 @@ def test_lowp_f32_storage_tracks_log_domain_iterates(ctx):
     f_or, g_or, _, _ = oracle.sinkhorn(C.astype(np.float64), p, q, 0.1, 0.0, 8)
     pi_or = oracle.plan(C.astype(np.float64), f_or, g_or, 0.1)
     np.testing.assert_allclose(_np(res.pi), pi_or, rtol=5e-5, atol=1e-12)
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("case", ["c1", "c4_sub"])
+def test_forced_absorption_matches_oracle(ctx, fmt, case):
+    C32, p, q, eps = _case_c1() if case == "c1" else _case_c4_sub()
+    C64 = C32.astype(np.float64)
+    res = ctx.solve_lowp(_t(C32), _t(p), _t(q), eps, tol=1e-6, max_iter=5000, fmt=_fmts()[fmt], absorb_log2=0.25)
+    assert res.absorptions > 0
+    assert res.status in (0, 1), res.status
+    f_or, g_or, _, _ = oracle.sinkhorn(C64, p, q, eps, 1e-9, 20000)
+    cost_or = oracle.finalize(C64, f_or, g_or, p, q, eps)[0]
+    cost, _, er, ec = oracle.finalize(C64, _np(res.f), _np(res.g), p, q, eps)
+    assert abs(res.transport_cost - cost_or) <= COST_TOL[fmt] * cost_or, (res.transport_cost, cost_or)
+    assert abs(cost - cost_or) <= COST_TOL[fmt] * cost_or
+    assert er <= MARG_TOL[fmt] and ec <= MARG_TOL[fmt], (er, ec)
+
+
+@pytest.mark.parametrize("case", ["c1", "c4_sub"])
+def test_natural_absorption_matches_oracle(ctx, case):
+    # FP16 storage at eps = 0.001 median(C): the scalings leave [2^-8, 2^8] under the default
+    # threshold, so K~ is rebuilt from C during the solve without being asked to
+    C32, p, q, eps = _case_c1() if case == "c1" else _case_c4_sub()
+    eps = eps / 50.0  # 0.05 -> 0.001 x median(C)
+    C64 = C32.astype(np.float64)
+    res = ctx.solve_lowp(_t(C32), _t(p), _t(q), eps, tol=1e-6, max_iter=5000, fmt=_fmts()["f16"])
+    assert res.absorptions >= 1
+    assert res.status in (0, 1), res.status
+    f_or, g_or, _, _ = oracle.sinkhorn(C64, p, q, eps, 1e-9, 20000)
+    cost_or = oracle.finalize(C64, f_or, g_or, p, q, eps)[0]
+    cost, _, er, ec = oracle.finalize(C64, _np(res.f), _np(res.g), p, q, eps)
+    assert abs(cost - cost_or) <= COST_TOL["f16"] * cost_or, (cost, cost_or)
+    assert er <= MARG_TOL["f16"] and ec <= MARG_TOL["f16"], (er, ec)
 
 
 @pytest.mark.parametrize("fmt", ["f32", "bf16", "f16"])

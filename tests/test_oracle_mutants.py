@@ -22,6 +22,8 @@ MUTANTS = {
     "rates_sign": ("interference += P[k] * g[k];", "interference -= P[k] * g[k];"),
     "rates_index": ("if (k != j) interference += P[k] * g[k];", "if (k != j) interference += P[j] * g[k];"),
     "rates_log": ("log1p(sinr) / log(2.0)", "log1p(sinr)"),
+    "rates_total_own": ("const double interference = ((t - own) + c) + N0;",
+                        "const double interference = (t + c) + N0;"),
     "cost_mu": ("C_out[t] = 1.0 / (mu * R[t]);", "C_out[t] = mu / R[t];"),
     "row_sign": ("y[j] = (g[j] - C[i * J + j]) / eps;", "y[j] = (g[j] + C[i * J + j]) / eps;"),
     "row_drop_logp": ("f[i] = eps * log(p[i]) - eps * lse_row(y, J);", "f[i] = - eps * lse_row(y, J);"),
@@ -35,6 +37,8 @@ MUTANTS = {
     "stop_early": ("if (err <= tol || k >= max_iter) break;", "if (err <= 10*tol || k >= max_iter) break;"),
     "norm_shift": ("double shift = eps * log(sp);", "double shift = 0.0;"),
     "finalize_rho": ("rho_out[j] = c;", "rho_out[j] = s;"),
+    "finalize_row_mass": ("*err_row_out = er / mass;", "*err_row_out = er;"),
+    "finalize_col_mass": ("*err_col_out = ec / mass;", "*err_col_out = ec;"),
     "maxsinr_tie": ("if (R[i * J + j] > R[i * J + best]) best = j;",
                     "if (R[i * J + j] >= R[i * J + best]) best = j;"),
     "adaptive_split": ("q[j] + d / (double)(J - 1);", "q[j] + d / (double)(J);"),

@@ -76,6 +76,25 @@ def test_rates_symmetric_pair():
     np.testing.assert_allclose(R[0], [math.log2(1 + s)] * 2, rtol=1e-14)
 
 
+def test_rates_total_form_equals_direct_sum():
+    """The O(I J) total-minus-own interference gives the direct sum's rates (Sec. II-A), on the
+    config-1 channel, on rows where one link carries nearly all of the received power, and on
+    a single-RRH row (no interference: SINR = P G / N0)."""
+    inst = ins.config1()
+    G = inst.G[:200].astype(np.float64)
+    R1 = oracle.rates(G, inst.P, inst.N0, inst.W_hz)
+    R2 = oracle.rates_total(G, inst.P, inst.N0, inst.W_hz)
+    np.testing.assert_allclose(R2, R1, rtol=1e-12)
+    rng = _rng(17)
+    Gd = rng.uniform(1e-12, 1e-10, (5, 9))
+    Gd[np.arange(5), rng.integers(0, 9, 5)] = 1e-3  # dominant links, SINR ~ 1e6
+    P = rng.uniform(0.5, 2.0, 9)
+    np.testing.assert_allclose(oracle.rates_total(Gd, P, 1e-13, 2e7), oracle.rates(Gd, P, 1e-13, 2e7), rtol=1e-9)
+    g1 = np.array([[3e-9]])
+    np.testing.assert_allclose(oracle.rates_total(g1, [2.0], 1e-12, 1e6), 1e6 * np.log2(1 + 2.0 * 3e-9 / 1e-12),
+                               rtol=1e-13)
+
+
 def test_cost_closed_form_and_validation():
     np.testing.assert_allclose(oracle.cost(np.array([[2.0, 4.0]]), 0.5), [[1.0, 0.5]], rtol=0)
     with pytest.raises(ValueError):
@@ -391,6 +410,33 @@ def test_finalize_on_product_plan():
     np.testing.assert_allclose(cost, p @ C @ q, rtol=1e-12)
     np.testing.assert_allclose(rho, q * (p @ C), rtol=1e-12)
     assert er < 1e-14 and ec < 1e-14
+
+
+def test_finalize_residuals_of_a_perturbed_plan_with_mass_three():
+    """Residuals are total absolute residuals per unit of mass (Sec. III-C; Eqs. (3)-(4)).
+
+    A separable cost C_ij = u_i + v_j and potentials f_i = u_i + eps log(p_i (1 + d_i)),
+    g_j = v_j + eps log(q_j / M) give the product plan pi_ij = p_i (1 + d_i) q_j / M with
+    M = sum p = sum q = 3.  Its rows are p_i (1 + d_i) and its columns q_j (1 + sum_i p_i d_i / M),
+    so the row and column L1 residuals divided by the mass are sum_i |p_i d_i| / M and
+    |sum_i p_i d_i| / M; the cost and loads follow from the product form."""
+    rng = _rng(16)
+    I, J, M = 11, 6, 3.0
+    u, v = rng.uniform(0, 4, I), rng.uniform(0, 4, J)
+    C = u[:, None] + v[None, :]
+    p, q = _balanced(rng, I, J)
+    p, q = M * p, M * q
+    d = rng.uniform(-0.2, 0.1, I)
+    eps = 0.4
+    f = u + eps * np.log(p * (1.0 + d))
+    g = v + eps * np.log(q / M)
+    cost, rho, er, ec = oracle.finalize(C, f, g, p, q, eps)
+    P, Q = p * (1.0 + d), q / M
+    np.testing.assert_allclose(er, np.abs(p * d).sum() / M, rtol=1e-12)
+    np.testing.assert_allclose(ec, abs((p * d).sum()) / M, rtol=1e-12)
+    assert er > 1e-3 and ec > 1e-3
+    np.testing.assert_allclose(cost, P @ u + P.sum() * (Q @ v), rtol=1e-12)
+    np.testing.assert_allclose(rho, Q * (P @ u + v * P.sum()), rtol=1e-12)
 
 
 # ------------------------------------------------------------------------- maxSINR / Lemma 1
