@@ -490,6 +490,15 @@ def run_gpu(args):
         }
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(inst)
+        if ws == 1 and args.sub_records:
+            # the batched and serving configurations, smaller than their own workloads so that the
+            # default run stays within minutes (--workload c3 / c5 run them at full size)
+            pool = _pool(min(16, os.cpu_count() or 1))
+            try:
+                line["batched"] = batched_record(ctx, pool, args.sub_c3_instances, 2, 3)
+                line["serving"] = serving_record(ctx, pool, args.c5_rate, args.sub_c5_seconds, args.c5_group)
+            finally:
+                pool.close()
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -580,16 +589,15 @@ def _timed(fn, stream):
     return out, e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)
 
 
-def run_c3(args):
-    """256 ragged instances (I ~ U{2000..60000}, J ~ U{64..1024}, channel as the 1000 x 50
-    configuration), eps = 0.05 median(C) each: the batched persistent launch (captured graph)
-    against the per-instance solver loop, same tolerance."""
-    from paper_1805_01559_gb300 import instances as ins
-    shapes = ins.config3_shapes()[: args.c3_instances]
-    pool = _pool(min(16, os.cpu_count() or 1))
+def batched_record(ctx, pool, n_instances: int, warmup: int, steps: int, autotune: bool = False):
+    """The first n ragged instances of the batched configuration (I ~ U{2000..60000},
+    J ~ U{64..1024}, channel as the 1000 x 50 configuration), eps = 0.05 median(C) each: the
+    batched persistent launch (captured graph) against the per-instance solver loop, same
+    tolerance."""
     import torch
     from paper_1805_01559_gb300 import binding
-    ctx = binding.Context(0)
+    from paper_1805_01559_gb300 import instances as ins
+    shapes = ins.config3_shapes()[:n_instances]
     dev = torch.device("cuda", 0)
     items = []
     t0 = time.perf_counter()
@@ -601,7 +609,6 @@ def run_c3(args):
         _, med = ctx.build_cost(R, mu, eps_rel=1.0, C_out=C)
         del Gd, R
         items.append(dict(C=C, p=torch.from_numpy(lam).to(dev), q=torch.from_numpy(q).to(dev), eps=0.05 * med))
-    pool.close()
     gen_s = time.perf_counter() - t0
     s = torch.cuda.current_stream()
     mk = lambda: [binding.Instance(C=x["C"], p=x["p"], q=x["q"], eps=x["eps"], tol=TOL, max_iter=MAX_ITER)
@@ -614,38 +621,53 @@ def run_c3(args):
     res = {}
     for name in ("plain", "batched", "batched_tuned"):
         if name == "batched_tuned":
-            if not args.autotune:
+            if not autotune:
                 continue
             t_tune = time.perf_counter()
             ctx.autotune(mk(), iters=6)
             res["tune_s"] = time.perf_counter() - t_tune
         b = ctx.batch(mk(), graph=True) if name != "plain" else None
         run = plain if b is None else (lambda: [r.iters for r in b.run()])
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             run()
         ms_all, its = [], None
-        for _ in range(args.steps):
+        for _ in range(steps):
             its, ms, _ = _timed(run, s)
             ms_all.append(ms)
         ms = statistics.median(ms_all)
         ci = sum(c * it for c, it in zip(cells, its))
         res[name] = {"ms": ms, "solves_per_s": len(items) / (ms / 1e3), "cells_iters_per_s": ci / (ms / 1e3),
                      "gbs_equiv": 4.0 * sum(c * (it + 2) for c, it in zip(cells, its)) / (ms / 1e3) / 1e9,
-                     "iters_total": int(sum(its))}
+                     "gbs_alg": 4.0 * ci / (ms / 1e3) / 1e9, "iters_total": int(sum(its))}
         if b is not None:
             b.close()
     best = res.get("batched_tuned", res["batched"])
     peak, peak_kind = _peaks()
+    return {"workload": f"c3_{len(items)}_ragged: batched persistent launch (graph) vs per-instance loop",
+            "instances": len(items), "cells": int(sum(cells)), "tol": TOL, "eps_rel": 0.05, "inputs_s": gen_s,
+            "solves_per_s_ratio": best["solves_per_s"] / res["plain"]["solves_per_s"], **res,
+            "roofline": {"bound": "hbm", "kernel": "sk_batch", "achieved": best["gbs_alg"], "peak": peak,
+                         "unit": "GB/s", "frac": best["gbs_alg"] / peak,
+                         "frac_incl_setup_finalize": best["gbs_equiv"] / peak, "traffic": None,
+                         "peak_kind": peak_kind}}
+
+
+def run_c3(args):
+    """256 ragged instances (I ~ U{2000..60000}, J ~ U{64..1024}, channel as the 1000 x 50
+    configuration), eps = 0.05 median(C) each: the batched persistent launch (captured graph)
+    against the per-instance solver loop, same tolerance."""
+    pool = _pool(min(16, os.cpu_count() or 1))
+    from paper_1805_01559_gb300 import binding
+    ctx = binding.Context(0)
+    rec = batched_record(ctx, pool, args.c3_instances, args.warmup, args.steps, args.autotune)
+    pool.close()
+    best = rec.get("batched_tuned", rec["batched"])
     line = {"metric": METRIC, "value": best["cells_iters_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"c3_{len(items)}_ragged: batched persistent launch (graph) vs per-instance loop",
-                       "instances": len(items), "cells": int(sum(cells)), "tol": TOL, "eps_rel": 0.05,
-                       "inputs_s": gen_s},
-            "batched_vs_plain": {"solves_per_s_ratio": best["solves_per_s"] / res["plain"]["solves_per_s"],
-                                 **{k: v for k, v in res.items()}},
-            "roofline": {"bound": "hbm", "kernel": "sk_batch", "achieved": best["gbs_equiv"], "peak": peak,
-                         "unit": "GB/s", "frac": best["gbs_equiv"] / peak, "traffic": None, "peak_kind": peak_kind}}
+            "config": {"workload": rec["workload"], "instances": rec["instances"], "cells": rec["cells"],
+                       "tol": TOL, "eps_rel": 0.05, "inputs_s": rec["inputs_s"]},
+            "batched_vs_plain": rec, "roofline": rec["roofline"]}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -725,85 +747,215 @@ def run_c4(args):
     return 0
 
 
-def run_c5(args):
-    """Serving: 64 cells (I in {5k, 20k, 80k}, J in {128, 512, 1024}), devices moving 1-30 m/s,
-    Poisson arrivals at args.c5_rate req/s for args.c5_seconds s, replayed in real time; each
-    request moves its cell's devices by the time since the cell's previous request and is
-    solved warm (eps fixed per cell at 0.05 median of its first instance)."""
+def _c5_cells(shapes, pool):
+    """Host data of the serving cells (drawn in a spawn pool): positions, velocities, RRHs,
+    traffic, marginal and the fixed shadowing of every link."""
     from multiprocessing import shared_memory
-    from paper_1805_01559_gb300 import instances as ins
-    shapes = ins.serving_cell_shapes(64)
-    pool = _pool(min(16, os.cpu_count() or 1))
-    import torch
-    from paper_1805_01559_gb300 import binding
-    ctx = binding.Context(0)
-    srv = ctx.server(group_ctas=args.c5_group)
-    t0 = time.perf_counter()
-    ids = []
+    cells = []
     gen = list(pool.imap(_gen_c5, shapes, chunksize=1))
-    pool.close()
     try:
         for d in gen:
             shm = shared_memory.SharedMemory(name=d["shm"])
-            sh = np.ndarray((d["I"], d["J"]), np.float32, buffer=shm.buf)
             try:
-                cid = srv.add_cell(d["I"], d["J"], 0.0, np.ones(d["J"]), d["lam"], d["q"], ins.MU_PER_BIT,
-                                   ins.noise_power_w(), ins.W_HZ, tol=TOL, max_iter=MAX_ITER, dev_xy=d["dev_xy"],
-                                   dev_v=d["vel"], rrh_xy=d["rrh_xy"], shadow_db=sh, side_m=d["side"], eps_rel=0.05)
+                d["shadow"] = np.ndarray((d["I"], d["J"]), np.float32, buffer=shm.buf).copy()
             finally:
-                del sh
                 shm.close()
                 shm.unlink()
                 d["shm"] = None
-            ids.append(cid)
+            cells.append(d)
     finally:
-        for d in gen:  # blocks not uploaded (an error above)
+        for d in gen:
             if d["shm"]:
                 try:
                     shared_memory.SharedMemory(name=d["shm"]).unlink()
                 except FileNotFoundError:
                     pass
-    gen_s = time.perf_counter() - t0
-    t_arr, cells = ins.poisson_arrivals(args.c5_rate, args.c5_seconds, len(ids), seed=0)
-    last = np.zeros(len(ids))
-    results = []
+    return cells
+
+
+def _lat_stats(lat_ms):
+    lat = np.asarray(lat_ms, dtype=np.float64)
+    if lat.size == 0:
+        return None
+    return {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
+            "mean": float(lat.mean())}
+
+
+def _arm_record(name, t0, t_end, lat, queue, device, errs, iters, failed, extra=None):
+    n = len(lat)
+    rec = {"arm": name, "requests": n + failed, "failed": failed,
+           "solves_per_s": n / max(t_end - t0, 1e-9), "latency_ms": _lat_stats(lat),
+           "queue_wait_ms": _lat_stats(queue), "device_ms": _lat_stats(device),
+           "marg_err_max": float(max(errs)) if errs else None,
+           "iters_mean": float(np.mean(iters)) if iters else None}
+    if extra:
+        rec.update(extra)
+    return rec
+
+
+def _serve_run(ctx, cells, t_arr, cidx, realtime: bool, group: int):
+    """The trace through the server (continuous batching, resident cells, warm starts).
+    realtime: submit each request at its arrival time; else submit the whole trace at once."""
+    import torch
+    from paper_1805_01559_gb300 import instances as ins
+    srv = ctx.server(group_ctas=group)
+    try:
+        ids = [srv.add_cell(d["I"], d["J"], 0.0, np.ones(d["J"]), d["lam"], d["q"], ins.MU_PER_BIT,
+                            ins.noise_power_w(), ins.W_HZ, tol=TOL, max_iter=MAX_ITER, dev_xy=d["dev_xy"],
+                            dev_v=d["vel"], rrh_xy=d["rrh_xy"], shadow_db=d["shadow"], side_m=d["side"],
+                            eps_rel=0.05) for d in cells]
+        last = np.zeros(len(ids))
+        results = []
+        torch.cuda.synchronize()
+        start = time.perf_counter()
+        t0_us = None
+        for t, c in zip(t_arr, cidx):
+            if realtime:
+                while time.perf_counter() - start < t:
+                    results += srv.poll()
+            dt = float(t - last[c]) if last[c] > 0 else 0.0
+            last[c] = t
+            srv.submit(ids[c], None, dt)
+        results += srv.drain(timeout_s=600)
+        st = srv.stats()
+    finally:
+        srv.close()
+    ok = [r for r in results if r.status in (0, 1)]
+    t0 = min(r.t_submit_us for r in results)
+    t_end = max(r.t_done_us for r in results)
+    return _arm_record("served" if realtime else "served_backlog", t0 / 1e6, t_end / 1e6,
+                       [(r.t_done_us - r.t_submit_us) / 1e3 for r in ok],
+                       [(r.t_start_us - r.t_submit_us) / 1e3 for r in ok],
+                       [(r.t_done_us - r.t_start_us) / 1e3 for r in ok],
+                       [max(r.marg_err_row, r.marg_err_col) for r in ok], [r.iters for r in ok],
+                       len(results) - len(ok),
+                       {"group_ctas": group, "resident_bytes": st["resident_bytes"], "launches": st["launches"]})
+
+
+def _plain_run(ctx, cells, t_arr, cidx, realtime: bool, fmt=None):
+    """The same trace through the plain per-instance entry points, one request at a time in
+    arrival order: ot_assoc_build_cost_mobile (devices moved by dt, C rebuilt) then a solve
+    warm-started from the cell's previous g -- ot_assoc_solve_cost (FP32 log domain) or, with
+    fmt, ot_assoc_solve_lowp (stored kernel K~ in that format)."""
+    import torch
+    from paper_1805_01559_gb300 import instances as ins
+    dev = torch.device("cuda", 0)
+    state = []
+    for d in cells:
+        I, J = d["I"], d["J"]
+        ld = (J + 3) // 4 * 4
+        st = {"xy": torch.from_numpy(np.ascontiguousarray(d["dev_xy"], np.float64)).to(dev),
+              "v": torch.from_numpy(np.ascontiguousarray(d["vel"], np.float64)).to(dev),
+              "rrh": torch.from_numpy(np.ascontiguousarray(d["rrh_xy"], np.float32)).to(dev),
+              "sh": torch.from_numpy(d["shadow"]).to(dev),
+              "P": torch.ones(J, dtype=torch.float32, device=dev),
+              "p": torch.from_numpy(np.ascontiguousarray(d["lam"], np.float32)).to(dev),
+              "q": torch.from_numpy(np.ascontiguousarray(d["q"], np.float32)).to(dev),
+              "C": torch.empty((I, ld), dtype=torch.float32, device=dev)[:, :J],
+              "f": torch.empty(I, dtype=torch.float64, device=dev),
+              "g": torch.zeros(J, dtype=torch.float64, device=dev), "warm": False}
+        _, st["eps"] = ctx.build_cost_mobile(st["xy"], st["v"], st["rrh"], st["sh"], st["P"], 0.0, d["side"],
+                                             ins.noise_power_w(), ins.W_HZ, ins.MU_PER_BIT, C_out=st["C"],
+                                             eps_rel=0.05)
+        state.append(st)
+    last = np.zeros(len(cells))
+    lat, queue, device, errs, iters = [], [], [], [], []
+    failed = 0
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
     start = time.perf_counter()
-    for t, c in zip(t_arr, cells):
-        while time.perf_counter() - start < t:
-            results += srv.poll()
+    for t, c in zip(t_arr, cidx):
+        if realtime:
+            while time.perf_counter() - start < t:
+                pass
+        t_begin = time.perf_counter() - start
+        d, st = cells[c], state[c]
         dt = float(t - last[c]) if last[c] > 0 else 0.0
         last[c] = t
-        srv.submit(ids[c], None, dt)
-    results += srv.drain(timeout_s=600)
-    wall = time.perf_counter() - start
+        ctx.build_cost_mobile(st["xy"], st["v"], st["rrh"], st["sh"], st["P"], dt, d["side"], ins.noise_power_w(),
+                              ins.W_HZ, ins.MU_PER_BIT, C_out=st["C"])
+        warm = st["g"] if st["warm"] else None
+        if fmt is None:
+            r = ctx.solve_cost(st["C"], st["p"], st["q"], st["eps"], tol=TOL, max_iter=MAX_ITER, warm_g=warm,
+                               f=st["f"], g=st["g"], want_load=False)
+        else:
+            r = ctx.solve_lowp(st["C"], st["p"], st["q"], st["eps"], tol=TOL, max_iter=MAX_ITER, fmt=fmt,
+                               warm_g=warm, want_load=False)
+            st["g"].copy_(r.g)
+        st["warm"] = True
+        t_done = time.perf_counter() - start
+        arrival = t if realtime else 0.0
+        if r.status in (0, 1):
+            lat.append(1e3 * (t_done - arrival))
+            queue.append(1e3 * (t_begin - arrival))
+            device.append(1e3 * (t_done - t_begin))
+            errs.append(max(r.marg_err_row, r.marg_err_col))
+            iters.append(r.iters)
+        else:
+            failed += 1
+    t_end = time.perf_counter() - start
+    name = ("plain" if fmt is None else "plain_bf16") + ("" if realtime else "_backlog")
+    return _arm_record(name, 0.0 if not realtime else float(t_arr[0]) if len(t_arr) else 0.0, t_end, lat, queue,
+                       device, errs, iters, failed)
+
+
+def serving_record(ctx, pool, rate: float, seconds: float, group: int, bf16: bool = True):
+    """Served (continuous batching) against plain per-instance solves on one Poisson trace over
+    the 64 serving cells, at the offered rate (latency) and as a backlog (capacity)."""
+    from paper_1805_01559_gb300 import binding
+    from paper_1805_01559_gb300 import instances as ins
+    shapes = ins.serving_cell_shapes(64)
+    t0 = time.perf_counter()
+    cells = _c5_cells(shapes, pool)
+    gen_s = time.perf_counter() - t0
+    t_arr, cidx = ins.poisson_arrivals(rate, seconds, len(cells), seed=0)
+    arms = [_serve_run(ctx, cells, t_arr, cidx, True, group), _serve_run(ctx, cells, t_arr, cidx, False, group),
+            _plain_run(ctx, cells, t_arr, cidx, True), _plain_run(ctx, cells, t_arr, cidx, False)]
+    if bf16:
+        arms.append(_plain_run(ctx, cells, t_arr, cidx, False, fmt=binding.OT_KERNEL_BF16))
+    by = {a["arm"]: a for a in arms}
+    cap_ratio = by["served_backlog"]["solves_per_s"] / by["plain_backlog"]["solves_per_s"]
+    return {"workload": f"c5_serving: 64 cells (I in {{5k, 20k, 80k}}, J in {{128, 512, 1024}}), Poisson "
+                        f"{rate:g} req/s for {seconds:g} s, devices moving 1-30 m/s, tol {TOL}",
+            "offered_per_s": len(t_arr) / seconds, "requests": int(len(t_arr)),
+            "served_vs_plain_capacity": cap_ratio, "arms": by, "inputs_s": gen_s,
+            "note": "served: ot_assoc_server_* (resident cells, warm starts, continuous batching in one "
+                    "persistent launch); plain: ot_assoc_build_cost_mobile + ot_assoc_solve_cost (or "
+                    "ot_assoc_solve_lowp BF16) per request in arrival order on one stream; backlog = the "
+                    "whole trace submitted at once (capacity); latency = done - arrival"}
+
+
+def run_c5(args):
+    """Serving: 64 cells (I in {5k, 20k, 80k}, J in {128, 512, 1024}), devices moving 1-30 m/s,
+    Poisson arrivals at args.c5_rate req/s for args.c5_seconds s, replayed in real time through
+    the server and through plain per-instance solves (and as a backlog through both, for
+    capacity); --c5-sweep adds the server at several offered rates (fractions of its capacity)."""
+    pool = _pool(min(16, os.cpu_count() or 1))
+    import torch  # noqa: F401
+    from paper_1805_01559_gb300 import binding
+    from paper_1805_01559_gb300 import instances as ins
+    ctx = binding.Context(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    rec = serving_record(ctx, pool, args.c5_rate, args.c5_seconds, args.c5_group)
+    sweep = []
+    if args.c5_sweep:
+        cells = _c5_cells(ins.serving_cell_shapes(64), pool)
+        cap = rec["arms"]["served_backlog"]["solves_per_s"]
+        for frac in (0.5, 0.8, 0.95):
+            t_arr, cidx = ins.poisson_arrivals(frac * cap, args.c5_seconds, len(cells), seed=1)
+            r = _serve_run(ctx, cells, t_arr, cidx, True, args.c5_group)
+            r["offered_fraction_of_capacity"] = frac
+            r["offered_per_s"] = len(t_arr) / args.c5_seconds
+            sweep.append(r)
+    pool.close()
     clk = clocks.stop()
-    lat = np.array([r.latency_us for r in results]) / 1e3
-    ok = [r for r in results if r.status in (0, 1)]
-    t_first = min(r.t_submit_us for r in results)
-    t_last = max(r.t_done_us for r in results)
-    solves_per_s = len(ok) / ((t_last - t_first) / 1e6)
-    its = np.array([r.iters for r in ok])
-    err = np.array([max(r.marg_err_row, r.marg_err_col) for r in ok])
-    cells_map = {cid: shapes[k] for k, cid in enumerate(ids)}
-    ci = sum(cells_map[r.cell][0] * cells_map[r.cell][1] * r.iters for r in ok)
-    st = srv.stats()
-    line = {"metric": "served solves/s", "value": solves_per_s, "unit": "solves/s", "n_gpus": 1, "steps": len(results),
-            "warmup": 0, "ms_per_step": float(np.mean(lat)), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"c5_serving: 64 cells, Poisson {args.c5_rate:g} req/s for {args.c5_seconds:g} s",
-                       "offered_per_s": len(t_arr) / args.c5_seconds, "requests": len(t_arr),
-                       "group_ctas": args.c5_group, "kernel": "FP32 log domain (stored-kernel serving not built)",
-                       "resident_bytes": st["resident_bytes"], "launches": st["launches"], "inputs_s": gen_s},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
-            "iters": {"mean": float(its.mean()), "p99": float(np.percentile(its, 99))},
-            "marg_err_max": float(err.max()), "failed": len(results) - len(ok),
-            "cells_iters_per_s": ci / ((t_last - t_first) / 1e6), "wall_s": wall, "clocks": clk}
+    served = rec["arms"]["served"]
+    line = {"metric": "served solves/s", "value": served["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": served["requests"], "warmup": 0, "ms_per_step": served["latency_ms"]["mean"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": rec["workload"], "group_ctas": args.c5_group},
+            "serving": rec, "load_sweep": sweep, "clocks": clk}
     print(json.dumps(line), flush=True)
-    srv.close()
     ctx.close()
     return 0
 
@@ -1116,7 +1268,12 @@ def main():
     ap.add_argument("--c4-rows", type=int, default=400_000)
     ap.add_argument("--c5-rate", type=float, default=2000.0)
     ap.add_argument("--c5-seconds", type=float, default=10.0)
-    ap.add_argument("--c5-group", type=int, default=19)
+    ap.add_argument("--c5-group", type=int, default=38)
+    ap.add_argument("--c5-sweep", action="store_true")
+    ap.add_argument("--sub-records", type=int, default=1,
+                    help="attach the batched and serving records to the default line (1) or not (0)")
+    ap.add_argument("--sub-c3-instances", type=int, default=64)
+    ap.add_argument("--sub-c5-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.profile_solves > 0:
         return run_profile_solve(args)

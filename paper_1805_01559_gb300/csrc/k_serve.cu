@@ -83,21 +83,99 @@ __device__ __forceinline__ void st_release_sys_u32(unsigned* p, unsigned v) {
     asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Received power P G of one link from the path-loss model with the link's fixed shadowing X
+// (dB), which adds to the path loss: G = 10^(-(PL0 + 10 n log10 d + X) / 10), evaluated as
+// 2^(a0 - X/10 log2(10) - (n/2) log2 d^2) on the SFU (a simulation input).
+__device__ __forceinline__ float sv_pl(float x, float y, float rx, float ry, float sh, float P) {
+    const float l2_10 = 3.3219280948873622f;  // log2(10)
+    const float a0 = -30.0f * 0.1f * l2_10;   // -PL0/10 log2(10), PL0 = 30 dB
+    const float half_n = 0.5f * 3.5f;         // n/2 with the path-loss exponent n = 3.5
+    const float dx = x - rx, dy = y - ry;
+    const float d2 = fmaxf(fmaf(dx, dx, dy * dy), 100.0f);  // d >= 10 m
+    const float e = fmaf(sh, -0.1f * l2_10, a0) - half_n * __log2f(d2);
+    return P * ex2(e);
+}
+
+// Received power P_j G_ij of one cell: the caller's gains, or the path-loss model.
+__device__ __forceinline__ float sv_power(const SvPrep& Q, int64_t i, int J, int j, float x, float y) {
+    if (Q.G) return Q.P[j] * __ldg(Q.G + i * Q.ld_g + j);
+    return sv_pl(x, y, Q.rrh_xy[2 * j], Q.rrh_xy[2 * j + 1], __ldg(Q.shadow + i * (int64_t)J + j), Q.P[j]);
+}
+
+// Rate (Sec. II-A, every other RRH interfering; the row total of received powers as the FP32
+// pair (hi, lo)) and cost C = 1 / (mu R) of a cell with received power pg; +inf (and bad set)
+// when the rate is not finite and > 0.
+__device__ __forceinline__ float sv_cost(const SvPrep& Q, float pg, float hi, float lo, int& bad) {
+    const float inv_ln2 = 1.4426950408889634f;
+    const float interf = ((hi - pg) + lo) + Q.N0;
+    const float R = Q.W * log1pf(__fdividef(pg, interf)) * inv_ln2;
+    const bool ok = R > 0.f && isfinite(R);
+    bad |= !ok;
+    return ok ? __frcp_rn(Q.mu * R) : INFINITY;
+}
+
+// One row in chunks of four columns (J a multiple of 4 and every row 16-byte aligned): a lane
+// owns chunks col = 4 (lane + 32 v), loads gains or shadowing, RRH coordinates and powers as
+// 16-byte vectors and keeps its received powers in registers between the pass that forms the
+// row total and the pass that writes the costs.
+template <int VPT>
+__device__ __forceinline__ void sv_row_vec(const SvPrep& Q, float* row, int J, int64_t i, float x, float y, int lane,
+                                           int& bad) {
+    float4 pw[VPT];
+    float hi = 0.f, lo = 0.f;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int col = 4 * (lane + 32 * v);
+        float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col < J) {
+            const float4 P4 = __ldg(reinterpret_cast<const float4*>(Q.P + col));
+            if (Q.G) {
+                const float4 g = __ldg(reinterpret_cast<const float4*>(Q.G + i * Q.ld_g + col));
+                p4 = make_float4(P4.x * g.x, P4.y * g.y, P4.z * g.z, P4.w * g.w);
+            } else {
+                const float4 s4 = __ldg(reinterpret_cast<const float4*>(Q.shadow + i * (int64_t)J + col));
+                const float4 ra = __ldg(reinterpret_cast<const float4*>(Q.rrh_xy + 2 * col));
+                const float4 rb = __ldg(reinterpret_cast<const float4*>(Q.rrh_xy + 2 * col + 4));
+                p4 = make_float4(sv_pl(x, y, ra.x, ra.y, s4.x, P4.x), sv_pl(x, y, ra.z, ra.w, s4.y, P4.y),
+                                 sv_pl(x, y, rb.x, rb.y, s4.z, P4.z), sv_pl(x, y, rb.z, rb.w, s4.w, P4.w));
+            }
+        }
+        pw[v] = p4;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float t, e2;
+            two_sum(hi, comp(p4, c), t, e2);
+            hi = t;
+            lo += e2;
+        }
+    }
+    warp_sum_pair(hi, lo);
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int col = 4 * (lane + 32 * v);
+        if (col < J) {
+            float4 o;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) comp(o, c) = sv_cost(Q, comp(pw[v], c), hi, lo, bad);
+            *reinterpret_cast<float4*>(row + col) = o;
+        }
+    }
+}
+
 // Rebuild the cost of rows [r0, r1) of a request's instance (all threads of the CTA, one warp
 // per row): positions moved by dt (drift mode; FP32 arithmetic, lanes 0 and 1 one axis each)
-// and gains from the path-loss model with the cell's fixed shadowing (in the form
-// 2^(a - (n/2) log2 d^2) on the SFU: a simulation input), or the caller's gains; then the
-// rates with every other RRH interfering (Sec. II-A; the row total of received powers as an
-// FP32 pair) and C = 1 / (mu R).  The first pass leaves the received powers in the cost row,
-// the second turns them into costs.  Invalid rates fail the request.
+// and received powers from the path-loss model with the cell's fixed shadowing, or the
+// caller's gains; then the rates with every other RRH interfering (Sec. II-A) and
+// C = 1 / (mu R).  Rows of up to 1024 columns whose arrays are 16-byte aligned go in float4
+// chunks (sv_row_vec); others column by column, the second pass recomputing each power.
+// Invalid rates fail the request.
 __device__ __forceinline__ void sv_rebuild_rows(const SvPrep& Q, float* C, int64_t ldc, int J, int64_t r0, int64_t r1,
                                                 int* status) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const float inv_ln2 = 1.4426950408889634f;
-    const float l2_10 = 3.3219280948873622f;  // log2(10)
-    const float a0 = -30.0f * 0.1f * l2_10;   // -PL0/10 log2(10), PL0 = 30 dB
-    const float half_n = 0.5f * 3.5f;         // log2 G = a0 - X/10 log2(10) - (n/2) log2 d^2
     const float side = (float)Q.side, dt = (float)Q.dt;
+    auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+    const bool vec = J <= 1024 && J % 4 == 0 && ldc % 4 == 0 && a16(C) && a16(Q.P) &&
+                     (Q.G ? (Q.ld_g % 4 == 0 && a16(Q.G)) : (a16(Q.shadow) && a16(Q.rrh_xy)));
     int bad = 0;
     for (int64_t i = r0 + warp; i < r1; i += nw) {
         float pos = 0.f;
@@ -113,33 +191,24 @@ __device__ __forceinline__ void sv_rebuild_rows(const SvPrep& Q, float* C, int64
         }
         const float x = __shfl_sync(0xffffffffu, pos, 0), y = __shfl_sync(0xffffffffu, pos, 1);
         float* row = C + i * ldc;
-        float hi = 0.f, lo = 0.f;
-        for (int j = lane; j < J; j += 32) {
-            float v;
-            if (Q.G) {
-                v = Q.P[j] * __ldg(Q.G + i * Q.ld_g + j);
-            } else {
-                const float dx = x - Q.rrh_xy[2 * j], dy = y - Q.rrh_xy[2 * j + 1];
-                const float d2 = fmaxf(fmaf(dx, dx, dy * dy), 100.0f);  // d >= 10 m
-                // shadowing X (dB) adds to the path loss: G = 10^(-(PL0 + 10 n log10 d + X) / 10)
-                const float e = fmaf(Q.shadow[i * (int64_t)J + j], -0.1f * l2_10, a0) - half_n * __log2f(d2);
-                v = Q.P[j] * ex2(e);
+        if (vec && J <= 128) {
+            sv_row_vec<1>(Q, row, J, i, x, y, lane, bad);
+        } else if (vec && J <= 256) {
+            sv_row_vec<2>(Q, row, J, i, x, y, lane, bad);
+        } else if (vec && J <= 512) {
+            sv_row_vec<4>(Q, row, J, i, x, y, lane, bad);
+        } else if (vec) {
+            sv_row_vec<8>(Q, row, J, i, x, y, lane, bad);
+        } else {
+            float hi = 0.f, lo = 0.f;
+            for (int j = lane; j < J; j += 32) {
+                float t, e2;
+                two_sum(hi, sv_power(Q, i, J, j, x, y), t, e2);
+                hi = t;
+                lo += e2;
             }
-            row[j] = v;
-            float t, e2;
-            two_sum(hi, v, t, e2);
-            hi = t;
-            lo += e2;
-        }
-        warp_sum_pair(hi, lo);
-        __syncwarp();
-        for (int j = lane; j < J; j += 32) {
-            const float pg = row[j];
-            const float interf = ((hi - pg) + lo) + Q.N0;
-            const float R = Q.W * log1pf(__fdividef(pg, interf)) * inv_ln2;
-            const bool ok = R > 0.f && isfinite(R);
-            bad |= !ok;
-            row[j] = ok ? __frcp_rn(Q.mu * R) : INFINITY;
+            warp_sum_pair(hi, lo);
+            for (int j = lane; j < J; j += 32) row[j] = sv_cost(Q, sv_power(Q, i, J, j, x, y), hi, lo, bad);
         }
     }
     if (bad) atomicCAS(status, DEV_OK, DEV_EINVAL);

@@ -1033,6 +1033,17 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             errt = 0.f;
             if (vp + 1 < v1) bar_named(CONS_BAR, NC);  // errf is read by thread 0 above
         }
+        // the constant per-column values of this thread's first round of column updates are
+        // loaded before the barrier, so only the totals cross L2 after it
+        constexpr int CU = 3;
+        float2 lq0[CU];
+        int sx0[CU];
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            const int j = tid + u * NC;
+            lq0[u] = j < J ? __ldcg(LQ2 + j) : make_float2(0.f, 0.f);
+            sx0[u] = j < J ? __ldcg(SX + j) : 0;
+        }
         OTA_BARRIER();
         // Loop test on pi^(s-1): every thread reads the same total of the row residuals.
         const double ed = (double)__ldcg(acc_s + Jp) * 0x1p-50;
@@ -1058,7 +1069,6 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
             int bad = 0;
             // CU columns a thread per round: all loads of a round first (one trip to L2), then
             // the arithmetic
-            constexpr int CU = 3;
             for (int j0 = tid; j0 < J; j0 += CU * NC) {
                 unsigned long long T[CU];
                 float2 lq[CU];
@@ -1067,8 +1077,8 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
                 for (int u = 0; u < CU; ++u) {
                     const int j = j0 + u * NC;
                     T[u] = j < J ? __ldcg(acc_s + j) : 0ull;
-                    lq[u] = j < J ? __ldcg(LQ2 + j) : make_float2(0.f, 0.f);
-                    sx[u] = j < J ? __ldcg(SX + j) : 0;
+                    lq[u] = j0 == tid ? lq0[u] : (j < J ? __ldcg(LQ2 + j) : make_float2(0.f, 0.f));
+                    sx[u] = j0 == tid ? sx0[u] : (j < J ? __ldcg(SX + j) : 0);
                 }
 #pragma unroll
                 for (int u = 0; u < CU; ++u) {
