@@ -759,8 +759,111 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
     bar_named(CONS_BAR, NC);
     int par = 0;
 
-    // ---- sweep 1: exact log-domain iteration ------------------------------------------
+    // ---- sweep 1: the log-domain iteration from G^0 with a fixed column scale --------------
+    // Every row of the half-step plan is normalised (t_ij = pi_ij / p_i <= 1 after the row
+    // shift), so the column sums of p^_i t_ij 2^64 cannot overflow: one ex2 a cell, like the
+    // later sweeps.  A column whose scaled sum falls below 2^-60 (a true sum below 2^-124) is
+    // marked, and then the whole first iteration is taken again in the exact form below (an
+    // online (max, sum) pair per column) on the next pass of the stream.
+    unsigned long long* flag1 = ACC + Jp + 1;  // zeroed with the totals in setup
+    bool exact1 = false;
     {
+        float4 acc[VPT];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2* F1 = Fs + S.rmax;  // F'^1 lives in buffer 1
+        int kb = 0;
+        for (int vp = v0; vp < v1; ++vp) {
+            const int vend = pend[vp];
+            for (; kb < vend; ++kb) {
+                const int st = (int)(cseq % (uint32_t)S.stages);
+                const uint32_t ph = (cseq / (uint32_t)S.stages) & 1u;
+                const bool ok = EUC || mbar_try_wait(&full[st], ph) || mbar_wait_bounded(&full[st], ph, P.spin, g.abort);
+                const int lr0 = kb * rs_;
+                const int rows = min(rs_, nrow - lr0);
+                const float* stage = ring + (size_t)st * S.stage_floats;
+                for (int j = 0; ok && j < S.rpt; ++j) {
+                    const int rr = tm.team + NTEAMS * j;
+                    if (rr >= rows) break;
+                    float4 x[VPT];
+                    if constexpr (EUC)
+                        euclid_row<TW, VPT>(__ldg(P.dev_xy + r0 + lr0 + rr), rxs, rxs + Jp, J, tm.tl, x);
+                    else
+                        load_row_smem<TW, VPT>(stage + (size_t)rr * P.ld, J, tm.tl, x);
+                    float m = -INFINITY;  // row maximum of G^0 - k C (approximate: only a shift)
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        const int col = 4 * (tm.tl + TT * v);
+                        float4 gv = col < Jp ? *reinterpret_cast<const float4*>(Gs + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) m = fmaxf(m, fmaf(-comp(x[v], c), P.k_hi, comp(gv, c)));
+                    }
+                    m = team_reduce<TW, float, true>(m, red, NTEAMS, tm, par);
+                    float sum = 0.f;
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        const int col = 4 * (tm.tl + TT * v);
+                        float4 gv = col < Jp ? *reinterpret_cast<const float4*>(Gs + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        float4 gl = col < Jp ? *reinterpret_cast<const float4*>(Gs + Jp + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float t = ex2(expo2(-m, comp(gl, c), comp(gv, c), comp(x[v], c), P.k_hi, P.k_lo));
+                            comp(x[v], c) = t;
+                            sum += t;
+                        }
+                    }
+                    sum = team_reduce<TW, float, false>(sum, red, NTEAMS, tm, par);
+                    const float ls = log2f(sum);
+                    if (tm.tl == 0) {  // F'^1 = -LSE2_j(y) = -(m + log2 sum), exact as an FP32 pair
+                        float hi, lo;
+                        two_sum(m, ls, hi, lo);
+                        F1[lr0 + rr] = make_float2(-hi, -lo);
+                    }
+                    const float w = __fdividef(Ps[lr0 + rr], sum) * 0x1p64f;  // p^_i 2^64 / sum
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        acc[v].x = fmaf(x[v].x, w, acc[v].x);
+                        acc[v].y = fmaf(x[v].y, w, acc[v].y);
+                        acc[v].z = fmaf(x[v].z, w, acc[v].z);
+                        acc[v].w = fmaf(x[v].w, w, acc[v].w);
+                    }
+                }
+                __syncwarp();
+                if (!EUC && lane == 0) mbar_arrive(&empty[st]);
+                ++cseq;
+            }
+            float* cp = P.colpart + (int64_t)vp * Jp;
+            cta_col_sum<TW, VPT>(comb, acc, J, Jp, tm, [&](int j, float sum) { cp[j] = sum; });
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        OTA_BARRIER();
+        // G^1_j = G^0_j + log2 q^_j - log2(column sum of pi^(1/2)), one warp per column
+        {
+            const int gw = b * NCW + warp, nw = nb * NCW;
+            for (int j = gw; j < J; j += nw) {
+                float2 sum = make_float2(0.f, 0.f);
+                for (int bb = lane; bb < V; bb += 32) sum = df_add(sum, P.colpart[(int64_t)bb * Jp + j]);
+                sum = warp_sum_df(sum);
+                if (lane == 0) {
+                    if (!(sum.x >= 0x1p-60f) || !isfinite(sum.x)) {
+                        atomicOr(flag1, 1ull);
+                    } else {
+                        const float2 ls = df_log2(sum);
+                        P.G[Jp + j] = P.G[j] + LQ[j] - (((double)ls.x - 64.0) + (double)ls.y);
+                    }
+                }
+            }
+        }
+        OTA_BARRIER_CHECK();
+        exact1 = __ldcg(flag1) != 0ull;
+        if (!exact1) {
+            load_G_smem(P.G + Jp, J, Jp, Gs, tid, NC);
+            bar_named(CONS_BAR, NC);
+        }
+    }
+    // ---- sweep 1 again, exact log-domain form (a column sum below the fixed scale's range) --
+    if (exact1) {
         float4 M[VPT], Sm[VPT];
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {

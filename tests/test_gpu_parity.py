@@ -176,6 +176,24 @@ def test_fixed_iterations_match_oracle(ctx, shape, iters):
                                rtol=RTOL_ITER, atol=1e-12)
 
 
+@pytest.mark.parametrize("iters", [1, 3])
+def test_first_iteration_with_an_underflowing_column(ctx, iters):
+    # Column 0 costs 3 more than any row's cheapest link at eps = 0.02: in the first half-step
+    # its entries are about 2^-216 of each row's largest, below the range of the first
+    # sweep's fixed 2^64 column scale, so the solver takes the first iteration again in the
+    # exact (online max, sum) form; the iterates still equal the oracle's.
+    I, J = 3000, 50
+    rng = _rng(77)
+    C = rng.uniform(0.0, 1.0, (I, J)).astype(np.float32)
+    C[:, 0] += 3.0
+    p, q = _marg(rng, I, J)
+    eps = 0.02
+    res = ctx.solve_cost(_t(C), _t(p), _t(q), eps, tol=0.0, max_iter=iters, want_pi=True)
+    f_or, g_or, _, _ = oracle.sinkhorn(C.astype(np.float64), p, q, eps, 0.0, iters)
+    assert res.iters == iters
+    _plan_check(_np(res.pi), C.astype(np.float64), f_or, g_or, eps, 1.0)
+
+
 @pytest.mark.parametrize("eps", [0.01, 0.02, 0.05, 0.1, 0.3, 1.0, 7.0])
 def test_forbidden_links_and_eps_values(ctx, eps):
     # +inf costs (no link) carry no mass for every eps; J = 45 leaves a masked tail chunk.
