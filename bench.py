@@ -781,19 +781,25 @@ def _lat_stats(lat_ms):
             "mean": float(lat.mean())}
 
 
-def _arm_record(name, t0, t_end, lat, queue, device, errs, iters, failed, extra=None):
+def _arm_record(name, t0, t_end, lat, queue, device, errs, iters, failed, extra=None, classes=None):
+    """classes: per request the size class (I x J) it belongs to, for latency per class."""
     n = len(lat)
     rec = {"arm": name, "requests": n + failed, "failed": failed,
            "solves_per_s": n / max(t_end - t0, 1e-9), "latency_ms": _lat_stats(lat),
            "queue_wait_ms": _lat_stats(queue), "device_ms": _lat_stats(device),
            "marg_err_max": float(max(errs)) if errs else None,
            "iters_mean": float(np.mean(iters)) if iters else None}
+    if classes is not None:
+        by = {}
+        for c, l in zip(classes, lat):
+            by.setdefault(c, []).append(l)
+        rec["latency_ms_by_class"] = {f"{c[0]}x{c[1]}": {**_lat_stats(v), "n": len(v)} for c, v in sorted(by.items())}
     if extra:
         rec.update(extra)
     return rec
 
 
-def _serve_run(ctx, cells, t_arr, cidx, realtime: bool, group: int):
+def _serve_run(ctx, cells, t_arr, cidx, realtime: bool, group: int, trace=None):
     """The trace through the server (continuous batching, resident cells, warm starts).
     realtime: submit each request at its arrival time; else submit the whole trace at once."""
     import torch
@@ -823,13 +829,17 @@ def _serve_run(ctx, cells, t_arr, cidx, realtime: bool, group: int):
     ok = [r for r in results if r.status in (0, 1)]
     t0 = min(r.t_submit_us for r in results)
     t_end = max(r.t_done_us for r in results)
+    cell_of = {cid: k for k, cid in enumerate(ids)}
+    if trace is not None:  # per request: cell, submitted, published, seen done (us), status
+        trace.extend((cell_of[r.cell], r.t_submit_us, r.t_start_us, r.t_done_us, r.status) for r in results)
     return _arm_record("served" if realtime else "served_backlog", t0 / 1e6, t_end / 1e6,
                        [(r.t_done_us - r.t_submit_us) / 1e3 for r in ok],
                        [(r.t_start_us - r.t_submit_us) / 1e3 for r in ok],
                        [(r.t_done_us - r.t_start_us) / 1e3 for r in ok],
                        [max(r.marg_err_row, r.marg_err_col) for r in ok], [r.iters for r in ok],
                        len(results) - len(ok),
-                       {"group_ctas": group, "resident_bytes": st["resident_bytes"], "launches": st["launches"]})
+                       {"group_ctas": group, "resident_bytes": st["resident_bytes"], "launches": st["launches"]},
+                       classes=[(cells[cell_of[r.cell]]["I"], cells[cell_of[r.cell]]["J"]) for r in ok])
 
 
 def _plain_run(ctx, cells, t_arr, cidx, realtime: bool, fmt=None):
@@ -859,7 +869,7 @@ def _plain_run(ctx, cells, t_arr, cidx, realtime: bool, fmt=None):
                                              eps_rel=0.05)
         state.append(st)
     last = np.zeros(len(cells))
-    lat, queue, device, errs, iters = [], [], [], [], []
+    lat, queue, device, errs, iters, classes = [], [], [], [], [], []
     failed = 0
     torch.cuda.synchronize()
     start = time.perf_counter()
@@ -890,12 +900,13 @@ def _plain_run(ctx, cells, t_arr, cidx, realtime: bool, fmt=None):
             device.append(1e3 * (t_done - t_begin))
             errs.append(max(r.marg_err_row, r.marg_err_col))
             iters.append(r.iters)
+            classes.append((d["I"], d["J"]))
         else:
             failed += 1
     t_end = time.perf_counter() - start
     name = ("plain" if fmt is None else "plain_bf16") + ("" if realtime else "_backlog")
     return _arm_record(name, 0.0 if not realtime else float(t_arr[0]) if len(t_arr) else 0.0, t_end, lat, queue,
-                       device, errs, iters, failed)
+                       device, errs, iters, failed, classes=classes)
 
 
 def serving_record(ctx, pool, rate: float, seconds: float, group: int, bf16: bool = True):
@@ -1180,10 +1191,11 @@ def run_euclid(args):
 
 
 def run_epsscale(args):
-    """eps-scaling on the 50,000 x 800 step's instance: Algorithm 1 at eps = 0.01 x median(C)
-    from b = 1 (sk_solve) against the same eps reached through the stages 0.1 -> 0.03 ->
-    0.01 x median (sk_eps_scaling, one launch, each stage warm-started from the previous
-    stage's g, intermediate stages to tol 1e-3, the last to the step's tol)."""
+    """eps-scaling on the 50,000 x 800 step's instance: Algorithm 1 at eps = e x median(C)
+    from b = 1 (sk_solve) against the same eps reached through the stages 0.1 -> 0.03 -> ...
+    -> e x median (sk_eps_scaling, one launch, each stage warm-started from the previous
+    stage's g, intermediate stages to tol 1e-3, the last to the step's tol), for every e in
+    --eps-final (the regime question: where do the stages pay)."""
     import torch
 
     from paper_1805_01559_gb300 import binding
@@ -1196,53 +1208,55 @@ def run_epsscale(args):
     lam = torch.from_numpy(inst.lam.astype(np.float32)).to(dev)
     q = torch.from_numpy(inst.q.astype(np.float32)).to(dev)
     C, med = ctx.build_cost_from_gains(G, P, inst.N0, inst.W_hz, inst.mu, eps_rel=1.0)
-    eps, eps0, factor = 0.01 * med, 0.1 * med, 0.3
+    eps0, factor = 0.1 * med, 0.3
     s = torch.cuda.current_stream()
-
-    def direct():
-        r = ctx.solve_cost(C, lam, q, eps, tol=TOL, max_iter=MAX_ITER)
-        return [r.iters], r.transport_cost
-
-    def staged():
-        r, stages = ctx.solve_eps_scaling(C, lam, q, eps, eps0, factor=factor, tol_stage=1e-3, tol=TOL,
-                                          max_iter=MAX_ITER)
-        return stages, r.transport_cost
-
-    for _ in range(args.warmup):
-        direct()
-        staged()
     clocks = ClockSampler(0)
     clocks.start()
-    l0 = ctx.launch_count()
-    out = {}
-    for name, fn in (("direct", direct), ("eps_scaling", staged)):
-        ms_all, its, cost = [], None, None
-        for _ in range(args.steps):
-            (its, cost), ms, _ = _timed(fn, s)
-            ms_all.append(ms)
-        ms = statistics.median(ms_all)
-        sweeps = sum(it + 2 for it in its)  # each stage: its iterations, the first and the finalize sweep
-        out[name] = {"ms": ms, "iters": its, "transport_cost": cost,
-                     "hbm_gbs": 4.0 * I * J * sweeps / (ms / 1e3) / 1e9}
-    launches = (ctx.launch_count() - l0) / (2 * args.steps)
-    clk = clocks.stop()
     peak, peak_kind = _peaks()
-    st = out["eps_scaling"]
+    regimes = []
+    for e_rel in [float(x) for x in args.eps_final.split(",")]:
+        eps = e_rel * med
+
+        def direct():
+            r = ctx.solve_cost(C, lam, q, eps, tol=TOL, max_iter=args.eps_max_iter)
+            return [r.iters], r.transport_cost, r.status
+
+        def staged():
+            r, stages = ctx.solve_eps_scaling(C, lam, q, eps, eps0, factor=factor, tol_stage=1e-3, tol=TOL,
+                                              max_iter=args.eps_max_iter)
+            return stages, r.transport_cost, r.status
+
+        for _ in range(args.warmup):
+            direct()
+            staged()
+        out = {}
+        for name, fn in (("direct", direct), ("eps_scaling", staged)):
+            ms_all, its, cost, st = [], None, None, None
+            for _ in range(args.steps):
+                (its, cost, st), ms, _ = _timed(fn, s)
+                ms_all.append(ms)
+            ms = statistics.median(ms_all)
+            sweeps = sum(it + 2 for it in its)  # each stage: its iterations, the first and the finalize sweep
+            out[name] = {"ms": ms, "iters": its, "transport_cost": cost, "status": st,
+                         "hbm_gbs": 4.0 * I * J * sweeps / (ms / 1e3) / 1e9}
+        regimes.append({"eps_rel": e_rel, **out, "speedup_vs_direct": out["direct"]["ms"] / out["eps_scaling"]["ms"],
+                        "cost_rel_diff": abs(out["direct"]["transport_cost"] - out["eps_scaling"]["transport_cost"])
+                        / out["direct"]["transport_cost"]})
+    clk = clocks.stop()
+    st = regimes[0]["eps_scaling"]
     line = {"metric": METRIC, "value": float(I) * J * sum(st["iters"]) / (st["ms"] / 1e3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": st["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "epsscale_50000x800: eps = 0.01 x median(C), direct vs stages 0.1 -> 0.03 -> 0.01",
+            "config": {"workload": "epsscale_50000x800: eps = e x median(C), direct vs stages from 0.1 x median",
                        "I": I, "J": J, "tol": TOL, "tol_stage": 1e-3, "factor": factor,
-                       "l2": "inputs larger than L2 (C 160 MB)"},
-            "solves": out,
-            "speedup_vs_direct": out["direct"]["ms"] / st["ms"],
+                       "max_iter": args.eps_max_iter, "l2": "inputs larger than L2 (C 160 MB)"},
+            "regimes": regimes,
             "roofline": {"bound": "hbm", "kernel": "sk_eps_scaling (whole call, CUDA events on its stream)",
                          "achieved": st["hbm_gbs"], "peak": peak, "unit": "GB/s",
-                         "frac": st["hbm_gbs"] / peak, "traffic": None, "peak_kind": peak_kind,
-                         "reads_of_C_per_launch": "sum over stages of (iters + 2)"},
-            "gpu_launches": launches, "clocks": clk}
-    ctx.close()
+                         "frac": st["hbm_gbs"] / peak, "traffic": None, "peak_kind": peak_kind},
+            "clocks": clk}
     print(json.dumps(line), flush=True)
+    ctx.close()
     return 0
 
 
@@ -1270,6 +1284,8 @@ def main():
     ap.add_argument("--c5-seconds", type=float, default=10.0)
     ap.add_argument("--c5-group", type=int, default=38)
     ap.add_argument("--c5-sweep", action="store_true")
+    ap.add_argument("--eps-final", default="0.01", help="final eps / median(C) values of --workload epsscale")
+    ap.add_argument("--eps-max-iter", type=int, default=MAX_ITER)
     ap.add_argument("--sub-records", type=int, default=1,
                     help="attach the batched and serving records to the default line (1) or not (0)")
     ap.add_argument("--sub-c3-instances", type=int, default=64)

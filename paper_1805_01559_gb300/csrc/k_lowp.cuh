@@ -167,16 +167,16 @@ __global__ void __launch_bounds__(256) lp_build(const float* __restrict__ C, int
 // RR: a row's values are read twice from the staged stage (once for the row sum, once for the
 // column partials) instead of being kept in registers, so a lane can hold twice the columns'
 // accumulators and rows of 4096 columns keep narrow teams (more rows in flight per CTA).
-template <typename T, int TW, int VPT, bool RR>
+// NCW: consumer warps of the block (teams of TW warps).
+template <typename T, int TW, int VPT, bool RR, int NCW>
 __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg& S, GroupCtx& g, SkShared* sh,
                                              unsigned char* dyn, int64_t r0, int64_t r1) {
     constexpr int N = Chunk<T>::N;
-    constexpr int NCW = Cons<TW>::NCW;
+    static_assert(NCW <= 24 && NCW / TW <= 12 && 2 * (NCW / TW) * TW <= 64, "SkShared sizes");
     constexpr int TT = 32 * TW, NTEAMS = NCW / TW, NC = NCW * 32;
-    constexpr int HALF = (NTEAMS + 1) / 2;
     uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
     uint64_t* empty = full + MAX_STAGES;
-    float* comb = reinterpret_cast<float*>(dyn + SMEM_HDR);   // [HALF][Jp]
+    float* comb = reinterpret_cast<float*>(dyn + SMEM_HDR);   // [Jp] merge row
     float* Bs = reinterpret_cast<float*>(dyn + S.off_G);      // [Jp] beta
     float* As = reinterpret_cast<float*>(dyn + S.off_F);      // [2][rmax] alpha
     float* Ps = reinterpret_cast<float*>(dyn + S.off_P);      // [rmax] p^
@@ -342,44 +342,32 @@ __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg&
                 if (lane == 0) mbar_arrive(&empty[st]);
                 ++cseq;
             }
-            // end of partition vp: column partials (teams in order) and row residual
+            // end of partition vp: column partials and row residual.  The teams add their
+            // partials into one merge row one team after the other (team order), so the
+            // shared memory of a second row goes to the ring instead.
             if (tm.tl == 0) sh->errf[tm.team] = errt;
-            if (tm.team < HALF) {
+            for (int t = 0; t < NTEAMS; ++t) {
+                if (tm.team == t) {
 #pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    const int col = N * (tm.tl + TT * v);
-                    if (col < Jp)
+                    for (int v = 0; v < VPT; ++v) {
+                        const int col = N * (tm.tl + TT * v);
+                        if (col < Jp)
 #pragma unroll
-                        for (int e = 0; e < N; e += 4)
-                            *reinterpret_cast<float4*>(comb + tm.team * Jp + col + e) =
-                                make_float4(acc[v][e], acc[v][e + 1], acc[v][e + 2], acc[v][e + 3]);
+                            for (int e = 0; e < N; e += 4) {
+                                float4* d = reinterpret_cast<float4*>(comb + col + e);
+                                float4 o = t == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : *d;
+                                o.x += acc[v][e];
+                                o.y += acc[v][e + 1];
+                                o.z += acc[v][e + 2];
+                                o.w += acc[v][e + 3];
+                                *d = o;
+                            }
+                    }
                 }
+                bar_named(CONS_BAR, NC);
             }
-            bar_named(CONS_BAR, NC);
-            if (tm.team >= HALF) {
-#pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    const int col = N * (tm.tl + TT * v);
-                    if (col < Jp)
-#pragma unroll
-                        for (int e = 0; e < N; e += 4) {
-                            float4* d = reinterpret_cast<float4*>(comb + (tm.team - HALF) * Jp + col + e);
-                            float4 o = *d;
-                            o.x += acc[v][e];
-                            o.y += acc[v][e + 1];
-                            o.z += acc[v][e + 2];
-                            o.w += acc[v][e + 3];
-                            *d = o;
-                        }
-                }
-            }
-            bar_named(CONS_BAR, NC);
             float* cp = P.colpart + (int64_t)vp * Jp;
-            for (int j = tid; j < J; j += NC) {
-                float sum = comb[j];
-                for (int t = 1; t < HALF; ++t) sum += comb[t * Jp + j];
-                cp[j] = sum;
-            }
+            for (int j = tid; j < J; j += NC) cp[j] = comb[j];
             if (tid == 0) {
                 float2 e = make_float2(sh->errf[0], 0.f);
                 for (int t = 1; t < NTEAMS; ++t) e = df_add(e, sh->errf[t]);
@@ -468,9 +456,8 @@ __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg&
 #undef LP_BARRIER
 }
 
-template <typename T, int TW, int VPT, bool RR>
-__global__ void __launch_bounds__(Cons<TW>::NT, 1) lp_loop(LpParams P, StreamCfg S) {
-    constexpr int NCW = Cons<TW>::NCW;
+template <typename T, int TW, int VPT, bool RR, int NCW>
+__global__ void __launch_bounds__(32 * (NCW + 1), 1) lp_loop(LpParams P, StreamCfg S) {
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ SkShared sh;
     uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
@@ -496,7 +483,7 @@ __global__ void __launch_bounds__(Cons<TW>::NT, 1) lp_loop(LpParams P, StreamCfg
         return;
     }
     GroupCtx g{(int)gridDim.x, (int)blockIdx.x, &P.st->bar, 0u, &P.st->status, &P.st->status};
-    lp_consumers<T, TW, VPT, RR>(P, S, g, &sh, dyn, r0, r1);
+    lp_consumers<T, TW, VPT, RR, NCW>(P, S, g, &sh, dyn, r0, r1);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -507,9 +494,9 @@ struct LpKernel {
     int tw, ncw;
 };
 
-template <typename T, int TW, int VPT, bool RR = false>
+template <typename T, int TW, int VPT, bool RR = false, int NCW = Cons<TW>::NCW>
 LpKernel lp_kernel() {
-    return LpKernel{(const void*)lp_loop<T, TW, VPT, RR>, TW, Cons<TW>::NCW};
+    return LpKernel{(const void*)lp_loop<T, TW, VPT, RR, NCW>, TW, NCW};
 }
 
 // One-warp teams while a lane holds at most 32 values (8 chunks of 4 or 4 of 8); 16-bit
@@ -555,10 +542,12 @@ ot_status lowp_solve_t(ot_assoc_ctx* ctx, const SolveArgs& a, double absorb_log2
     StreamCfg S;
     size_t smem = 0;
     int V = 1;
-    if (!plan_stage(nteams, I, Jp, ldk, 1, 24576, (size_t)1 << 40, &S, &smem, &V, (int)sizeof(T), 1))
+    // one float a row per scaling buffer, and one merge row for the teams' column partials
+    // (merged team after team): the room goes to the ring of stages
+    if (!plan_stage(nteams, I, Jp, ldk, 1, 24576, (size_t)1 << 40, &S, &smem, &V, (int)sizeof(T), 1, 4, 1))
         return set_error(ctx, OT_EUNSUPPORTED, "stored-kernel geometry");
     const int grid = std::max(1, std::min(V, ctx->num_sms));
-    if (!plan_stage(nteams, I, Jp, ldk, grid, 24576, 232448 - 4096, &S, &smem, &V, (int)sizeof(T), 1))
+    if (!plan_stage(nteams, I, Jp, ldk, grid, 24576, 232448 - 4096, &S, &smem, &V, (int)sizeof(T), 1, 4, 1))
         return set_error(ctx, OT_EUNSUPPORTED, "stored kernel does not fit the shared memory (I=%lld J=%d)",
                          (long long)I, J);
     if (allow_max_dynamic_smem(kk.fn, smem) != cudaSuccess) {

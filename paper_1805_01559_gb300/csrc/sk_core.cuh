@@ -339,13 +339,17 @@ __host__ __device__ __forceinline__ int parts_for(int64_t I, int rs) {
 }
 
 // Stage geometry and shared-memory layout of an instance solved by nb CTAs with teams of
-// `nteams` rows (g_words floats per column at off_G: 2 for the FP32 pairs of G).  The rows per stage depend only on the stage target and the row length,
+// `nteams` rows (g_words floats per column at off_G: 2 for the FP32 pairs of G; f_bytes per
+// row in each of the two row-potential buffers: an FP32 pair, or one float for the stored
+// kernel's scalings).  The rows per stage depend only on the stage target and the row length,
 // and the partitions only on I and the rows per stage: the arithmetic of a solve is fixed
 // by (I, J, ld, stage target) whatever nb is.  Returns false when a CTA's rows do not fit
 // next to two stages.
 inline bool plan_stage(int nteams, int64_t I, int Jp, int64_t ld, int nb, int stage_target, size_t budget,
-                       StreamCfg* S, size_t* smem, int* Vout, int esize = 4, int g_words = 2) {
-    const size_t comb = (size_t)((nteams + 1) / 2) * Jp * sizeof(float);
+                       StreamCfg* S, size_t* smem, int* Vout, int esize = 4, int g_words = 2,
+                       int f_bytes = (int)sizeof(float2), int comb_bufs = 0) {
+    // comb_bufs: rows of Jp floats for merging the teams' column partials (0: half the teams)
+    const size_t comb = (size_t)(comb_bufs > 0 ? comb_bufs : (nteams + 1) / 2) * Jp * sizeof(float);
     const size_t row_bytes = (size_t)ld * esize;
     const int rpt = (int)(stage_target / ((size_t)nteams * row_bytes) > 1 ? stage_target / ((size_t)nteams * row_bytes)
                                                                            : 1);
@@ -360,7 +364,7 @@ inline bool plan_stage(int nteams, int64_t I, int Jp, int64_t ld, int nb, int st
     auto up = [](size_t x, size_t m) { return (x + m - 1) / m * m; };
     const size_t off_G = up(SMEM_HDR + comb, 16);
     const size_t off_F = up(off_G + (size_t)g_words * Jp * sizeof(float), 16);  // G pairs: hi, then lo
-    const size_t off_P = off_F + (size_t)2 * rmax * sizeof(float2);
+    const size_t off_P = up(off_F + (size_t)2 * rmax * f_bytes, 16);  // two row-potential buffers
     const size_t off_ring = up(off_P + (size_t)rmax * sizeof(float), 128);
     const size_t stage = (size_t)rs * row_bytes;
     const size_t room = off_ring < budget ? (budget - off_ring) / stage : 0;
@@ -397,7 +401,7 @@ __device__ __forceinline__ void warp_sum_pair(float& s, float& e) {
 struct SkShared {
     float red[64];          // team reductions: 2 * NTEAMS * TW <= 24 values (float2 pairs: 48 floats)
     float errf[12];         // per-team row residuals
-    double sh_sum[12][2];   // per-warp setup sums
+    double sh_sum[24][2];   // per-warp setup sums (up to 24 consumer warps)
     int s_dec, s_ok, s_bad;
     volatile int s_stop;    // consumers -> producer: stop streaming
     int pend[VMAX + 1];     // stage blocks (from the CTA's first row) at which its partitions end
