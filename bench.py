@@ -6,9 +6,15 @@ lognormal(0, 1.5) traffic, capacity-proportional RRH marginal) with gains reside
 rates (Sec. II-A) and cost C = 1/(mu R) in one pass, the median of C -> three Sinkhorn solves
 (Algorithm 1, FP32 log domain, tol 1e-6, <= 2000 iterations) at eps = {0.1, 0.03, 0.01} x
 median(C), each with its FP64 finalize, enqueued back to back through the asynchronous API
-(--multi: the two smaller eps in one launch that shares each read of C, sk_solve_multi).  Metric: Sinkhorn cells x iterations per second
-over the whole step.  C (160 MB) is larger than the 126 MB L2, so no flush is needed
-between steps.
+(--multi: the two smaller eps in one launch that shares each read of C, sk_solve_multi).
+Metric: Sinkhorn cells x iterations per second over the whole step.  C (160 MB) is larger
+than the 126 MB L2, so no flush is needed between steps.
+
+On one GPU the line also carries three records (--sub-records 0 leaves them out):
+  batched    64 ragged instances, the batched persistent launch against a loop of solves;
+  serving    one Poisson trace through the server and through plain per-instance calls;
+  precision  the 400,000 x 4,096 instance, FP32 log domain against BF16 and FP16 K~.
+--workload selects the full-size form of one of them (or another workload) instead.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl gb300|reference]
 
@@ -497,6 +503,7 @@ def run_gpu(args):
             try:
                 line["batched"] = batched_record(ctx, pool, args.sub_c3_instances, 2, 3)
                 line["serving"] = serving_record(ctx, pool, args.c5_rate, args.sub_c5_seconds, args.c5_group)
+                line["precision"] = precision_record(ctx, pool, args.c4_rows, 1)
             finally:
                 pool.close()
         print(json.dumps(line), flush=True)
@@ -673,16 +680,14 @@ def run_c3(args):
     return 0
 
 
-def run_c4(args):
+def precision_record(ctx, pool, rows: int, warmup: int):
     """The 400,000 x 4,096 instance (16 km^2, hot spots, capacity q), eps = 0.05 median(C):
     the log-domain FP32 solver against the stored-kernel solver with K~ in BF16 and FP16."""
-    from paper_1805_01559_gb300 import instances as ins
-    I, J, block = args.c4_rows, 4096, 8192
-    inst = ins.config4_blocked(0, I, J, block)
-    pool = _pool(min(16, os.cpu_count() or 1))
     import torch
     from paper_1805_01559_gb300 import binding
-    ctx = binding.Context(0)
+    from paper_1805_01559_gb300 import instances as ins
+    I, J, block = rows, 4096, 8192
+    inst = ins.config4_blocked(0, I, J, block)
     dev = torch.device("cuda", 0)
     P = torch.from_numpy(inst.P.astype(np.float32)).to(dev)
     C = torch.empty((I, J), dtype=torch.float32, device=dev)
@@ -691,10 +696,8 @@ def run_c4(args):
     for b, G in pool.imap_unordered(_gen_c4_block, jobs):
         r0 = b * block
         Gd = torch.from_numpy(G).to(dev)
-        R = ctx.build_rates(Gd, P, inst.N0, inst.W_hz)
-        ctx.build_cost(R, inst.mu, C_out=C[r0:r0 + G.shape[0]])
-        del Gd, R
-    pool.close()
+        ctx.build_cost_from_gains(Gd, P, inst.N0, inst.W_hz, inst.mu, C_out=C[r0:r0 + G.shape[0]])
+        del Gd
     gen_s = time.perf_counter() - t0
     med = ctx.median_f32(C.view(-1))
     eps = 0.05 * med
@@ -709,16 +712,16 @@ def run_c4(args):
                                                        fmt=binding.OT_KERNEL_BF16)),
                      ("f16_K", lambda: ctx.solve_lowp(C, p, q, eps, tol=TOL, max_iter=MAX_ITER,
                                                       fmt=binding.OT_KERNEL_F16))):
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(1, warmup)):
             fn()
         r, ms, _ = _timed(fn, s)
         t = ctx.last_timings()
         if ref is None:
             ref = r
-        # the solver's persistent loop: C (4 bytes a cell) iters + 2 times for the log domain,
-        # K~ (2 bytes a cell) once per loop iteration and once to test for the stored kernel
+        # the solver's persistent loop: C (4 bytes a cell) once per iteration for the log domain,
+        # K~ (2 bytes a cell) once per loop iteration for the stored kernel
         if name == "f32_log":
-            loop_bytes = 4.0 * I * J * (t["sweeps"] + 2)
+            loop_bytes = 4.0 * I * J * r.iters
         else:
             loop_bytes = 2.0 * I * J * t["sweeps"]
         loop_gbs = loop_bytes / (t["loop_ms"] / 1e3) / 1e9 if t["valid"] and t["loop_ms"] > 0 else None
@@ -729,19 +732,36 @@ def run_c4(args):
                      "cells_iters_per_s": I * J * r.iters / (ms / 1e3), "transport_cost": r.transport_cost,
                      "cost_rel_vs_f32": abs(r.transport_cost - ref.transport_cost) / ref.transport_cost,
                      "marg_err_row": r.marg_err_row, "marg_err_col": r.marg_err_col, "status": r.status}
-    best = out["bf16_K"]
+    del C
+    torch.cuda.empty_cache()
     peak, peak_kind = _peaks()
+    best = out["bf16_K"]
     roof = None
     if best["loop_gbs"]:
         roof = {"bound": "hbm", "kernel": "lp_loop (stored BF16 kernel, 2 bytes a cell and iteration)",
                 "achieved": best["loop_gbs"], "peak": peak, "unit": "GB/s", "frac": best["loop_gbs"] / peak,
                 "traffic": None, "peak_kind": peak_kind}
+    return {"workload": f"c4_{I}x{J}: stored-kernel BF16/FP16 vs log-domain FP32", "I": I, "J": J, "eps": eps,
+            "tol": TOL, "inputs_s": gen_s, "formats": out,
+            "bf16_speedup_vs_f32": out["f32_log"]["ms"] / out["bf16_K"]["ms"], "roofline": roof,
+            "note": "marginal errors are the device's FP64 evaluation of the returned potentials on the true C "
+                    "(the whole-instance comparison with the FP64 oracle is a test)"}
+
+
+def run_c4(args):
+    """The 400,000 x 4,096 instance: FP32 log domain against BF16 and FP16 stored kernels."""
+    pool = _pool(min(16, os.cpu_count() or 1))
+    from paper_1805_01559_gb300 import binding
+    ctx = binding.Context(0)
+    rec = precision_record(ctx, pool, args.c4_rows, args.warmup)
+    pool.close()
+    best = rec["formats"]["bf16_K"]
     line = {"metric": METRIC, "value": best["cells_iters_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
             "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16 K~ (FP32 accumulation)", "data": "synthetic",
-            "config": {"workload": f"c4_{I}x{J}: stored-kernel BF16/FP16 vs log-domain FP32",
-                       "I": I, "J": J, "eps": eps, "tol": TOL, "inputs_s": gen_s},
-            "formats": out, "roofline": roof}
+            "config": {"workload": rec["workload"], "I": rec["I"], "J": rec["J"], "eps": rec["eps"], "tol": TOL,
+                       "inputs_s": rec["inputs_s"]},
+            "formats": rec["formats"], "roofline": rec["roofline"]}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
