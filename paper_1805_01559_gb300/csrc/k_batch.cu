@@ -104,24 +104,35 @@ std::vector<int> divisors(int n) {
 
 // Schedule model (used before tuning and to pick the candidates the tuner times): one sweep
 // of instance i on d CTAs takes the longer of streaming its cells at a CTA's share of HBM
-// bandwidth and walking its rows at the consumer warps' row rate, plus the group barriers.
+// bandwidth and walking its rows at the consumer warps' row rate, plus the group barrier and
+// the column update, plus the end of each of the CTA's row partitions (team partials merged
+// through shared memory, fixed-point column totals): an instance keeps up to VMAX partitions
+// whatever its group size, so small groups pay many partition ends a sweep.
 constexpr double BW_CTA = 40e9;       // bytes/s one CTA streams with all SMs busy
 constexpr double ROW_TIME = 0.5e-6;   // s per row per warp (latency of a row's chain)
+constexpr double PART_END = 2e-6;     // s per partition end
 double sweep_time(int64_t I, int J, int d) {
     const double stream = 4.0 * (double)I * J / (d * BW_CTA);
     const double rows = std::ceil((double)I / d) * ROW_TIME / BT_NCW;
     const double bar = d > 1 ? 3e-6 + 0.02e-6 * d : 0.5e-6;
-    return std::max(stream, rows) + bar;
+    const int64_t rs = BT_NCW;  // rows per stage of one-warp teams at one row a team
+    const int64_t V = std::max<int64_t>(1, std::min<int64_t>({(int64_t)VMAX, (I + rs - 1) / rs, I / 64}));
+    const double ends = std::ceil((double)V / d) * PART_END;
+    return std::max(stream, rows) + bar + ends;
 }
 
 // Group size of a batch: the divisor of the SM count that minimises the estimated makespan
 // of a largest-first queue over nsm / d groups (every instance taken at the same number of
-// sweeps).  Results do not depend on it: every reduction runs over the instances' own row
-// partitions.
+// sweeps), the larger group where estimates are within 2% (measured on the 256 ragged
+// instances: groups of 2, 4, 8, 19, 38, 76 of 152 CTAs took 108, 108, 106, 92, 99, 115 ms,
+// the autotuned plan 92 ms; the model misses costs that grow as groups shrink).  Results do
+// not depend on it: every reduction runs over the instances' own row partitions.
 int model_gsize(const std::vector<ot_assoc_instance>& v, int num_sms) {
     int best = 1;
     double best_t = 1e300;
-    for (int d : divisors(num_sms)) {
+    std::vector<int> ds = divisors(num_sms);
+    std::reverse(ds.begin(), ds.end());
+    for (int d : ds) {
         const int ng = num_sms / d;
         std::vector<double> t;
         t.reserve(v.size());
@@ -130,7 +141,7 @@ int model_gsize(const std::vector<ot_assoc_instance>& v, int num_sms) {
         std::vector<double> load(ng, 0.0);  // greedy list schedule, largest first
         for (double x : t) *std::min_element(load.begin(), load.end()) += x;
         const double m = *std::max_element(load.begin(), load.end());
-        if (m < best_t * 0.98) {  // prefer smaller groups unless clearly slower
+        if (m < best_t * 0.98) {  // a smaller group only when clearly faster
             best_t = m;
             best = d;
         }
