@@ -121,16 +121,38 @@ struct Chunk<__half> {
     }
 };
 
-// Build K~ from C at potentials (F', G): one warp per row, each lane a stride of 16-byte
-// output chunks; columns J..ldk-1 are written as 0.  Also records the references
-// F^' = F', G^ = G.  Dynamic shared memory: Jp floats (G rounded to FP32, as the
-// log-domain sweeps use it).
+// Four stored values (columns 4q .. 4q+3): 16 bytes for FP32, 8 for the 16-bit formats,
+// rounded pair by pair as the 16-byte chunk stores round them.
+template <typename T>
+__device__ __forceinline__ void store_quad(T* dst, const float (&v)[4]);
+template <>
+__device__ __forceinline__ void store_quad<float>(float* dst, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store_quad<__nv_bfloat16>(__nv_bfloat16* dst, const float (&v)[4]) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+    *reinterpret_cast<uint2*>(dst) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+template <>
+__device__ __forceinline__ void store_quad<__half>(__half* dst, const float (&v)[4]) {
+    const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+    *reinterpret_cast<uint2*>(dst) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+
+// Build K~ from C at potentials (F', G): one warp per row; lane l takes the column quads
+// l, l + 32, ... (consecutive lanes on consecutive 16-byte pieces of the row, BUILD_U quads a
+// lane in flight); columns J..ldk-1 are written as 0.  C is read in float4 pieces when its
+// rows are 16-byte aligned, else element by element.  Also records the references
+// F^' = F', G^ = G.  Dynamic shared memory: G as FP32 pairs (2 Jp floats).
+constexpr int BUILD_U = 4;
 template <typename T>
 __global__ void __launch_bounds__(256) lp_build(const float* __restrict__ C, int64_t ldc, T* __restrict__ K,
                                                 int64_t ldk, int64_t I, int J, int Jp, const float2* __restrict__ F,
                                                 const double* __restrict__ G, float2* Fref, double* Gref,
                                                 float k_hi, float k_lo) {
-    constexpr int N = Chunk<T>::N;
     extern __shared__ float Gs_build[];  // G as FP32 pairs: high parts, then low parts
     for (int j = threadIdx.x; j < Jp; j += blockDim.x) {
         const double x = j < J ? G[j] : 0.0;
@@ -144,20 +166,41 @@ __global__ void __launch_bounds__(256) lp_build(const float* __restrict__ C, int
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int nch = (int)((ldk + N - 1) / N);
+    const int nq = (int)(ldk >> 2);  // ldk is a multiple of 4 (of 8 for the 16-bit formats)
+    const bool vec = ((reinterpret_cast<uintptr_t>(C) | (uintptr_t)(ldc * (int64_t)sizeof(float))) & 15) == 0;
     for (int64_t i = w0; i < I; i += nw) {
         const float2 Fi = F[i];
         if (lane == 0) Fref[i] = Fi;
         const float* row = C + i * ldc;
         T* out = K + i * ldk;
-        for (int ch = lane; ch < nch; ch += 32) {
-            float v[N];
+        for (int q0 = lane; q0 < nq; q0 += 32 * BUILD_U) {
+            float4 c[BUILD_U];
 #pragma unroll
-            for (int e = 0; e < N; ++e) {
-                const int j = ch * N + e;
-                v[e] = j < J ? ex2(expo2(Fi.x, Fi.y + Gs_build[Jp + j], Gs_build[j], __ldg(row + j), k_hi, k_lo)) : 0.f;
+            for (int u = 0; u < BUILD_U; ++u) {  // every load of the round first
+                const int col = 4 * (q0 + 32 * u);
+                if (vec && col + 3 < J) {
+                    c[u] = __ldg(reinterpret_cast<const float4*>(row + col));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) comp(c[u], e) = col + e < J ? __ldg(row + col + e) : 0.f;
+                }
             }
-            Chunk<T>::store(out + (int64_t)ch * N, v);
+#pragma unroll
+            for (int u = 0; u < BUILD_U; ++u) {
+                const int q = q0 + 32 * u;
+                if (q >= nq) break;
+                const int col = 4 * q;
+                float v[4] = {0.f, 0.f, 0.f, 0.f};
+                if (col < J) {  // col + 3 < Jp
+                    const float4 gh = *reinterpret_cast<const float4*>(Gs_build + col);
+                    const float4 gl = *reinterpret_cast<const float4*>(Gs_build + Jp + col);
+                    const float ghv[4] = {gh.x, gh.y, gh.z, gh.w}, glv[4] = {gl.x, gl.y, gl.z, gl.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (col + e < J) v[e] = ex2(expo2(Fi.x, Fi.y + glv[e], ghv[e], comp(c[u], e), k_hi, k_lo));
+                }
+                store_quad<T>(out + col, v);
+            }
         }
     }
 }

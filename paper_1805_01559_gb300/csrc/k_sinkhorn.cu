@@ -396,6 +396,7 @@ cudaError_t enqueue_solve(const SolveArgs& a, const Kernels& kk, const LoopLaunc
     P.k_lo = k_lo;
     P.tol = mode.init ? 0.0 : a.tol;
     P.max_iter = mode.init ? 1 : a.max_iter;
+    P.init_only = mode.init;
     P.spin = spin;
     P.fpart = mode.init ? nullptr : B.fpart;
     P.epart = B.errpart + LL.V;

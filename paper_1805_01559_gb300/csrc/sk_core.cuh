@@ -304,6 +304,9 @@ struct SolveParams {
     // ring's offset (x then y, Jp floats each).
     const float2* dev_xy;  // [I]
     const float2* rrh_xy;  // [J]
+    // Iteration 1 only (the stored-kernel form starts from its potentials): F'^1 to F_out and
+    // G^1 in G + Jp, no test sweep and no finalize.
+    int init_only = 0;
 };
 
 // Row partitions.  The I rows form B = ceil(I / rs) stage blocks of rs rows; partition v of V
@@ -567,9 +570,13 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
         ++cseq;
         const bool at_end = (kb + 1 == vend);
         if ((kb + 1 - vbeg) % every == 0 || at_end) {
+            // Reductions without a returned value: the thread that zeroed fp[j] is the one that
+            // adds to it, flush after flush, so the sums are the serial ones, bit for bit, but no
+            // thread waits on L2 for the old value (at 4,096 columns a read-modify-write per
+            // column made the flushes cost as much as the sweep).
             double2* fp = P.fpart + (int64_t)vp * Jp;
-            cta_col_sum<TW, VPT>(comb, cpi, J, Jp, tm, [&](int j, float sum) { fp[j].x += (double)sum; });
-            cta_col_sum<TW, VPT>(comb, crho, J, Jp, tm, [&](int j, float sum) { fp[j].y += (double)sum; });
+            cta_col_sum<TW, VPT>(comb, cpi, J, Jp, tm, [&](int j, float sum) { atomicAdd(&fp[j].x, (double)sum); });
+            cta_col_sum<TW, VPT>(comb, crho, J, Jp, tm, [&](int j, float sum) { atomicAdd(&fp[j].y, (double)sum); });
 #pragma unroll
             for (int v = 0; v < VPT; ++v) cpi[v] = crho[v] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -1047,6 +1054,19 @@ __device__ __forceinline__ bool sk_consumers(const SolveParams& P, const StreamC
         OTA_BARRIER_CHECK();
         load_G_smem(P.G + Jp, J, Jp, Gs, tid, NC);
         bar_named(CONS_BAR, NC);
+    }
+
+    if (P.init_only) {  // iteration 1 is all that was asked for: no sweep to test its plan
+        if (P.F_out)
+            for (int r = tid; r < nrow; r += NC) P.F_out[r0 + r] = Fs[S.rmax + r];
+        if (b == 0 && tid == 0) {
+            P.st->iters = 1;
+            P.st->err = 0.0;
+            P.st->converged = 0;
+        }
+        *ret_par = 1;
+        if (tid == 0) s_stop = 1;
+        return true;
     }
 
     // ---- sweeps 2, 3, ...: one read of C and one ex2 per cell -----------------------------
