@@ -518,6 +518,16 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
     const int nblk = (nrow + rs_ - 1) / rs_;
     const bool want_pi = P.pi != nullptr;
     const int every = max(1, FIN_ROWS / S.rpt);  // stages between flushes
+    // Multi-warp teams: a row's sum is reduced within each warp (shuffles only) and the warps'
+    // pairs wait in the merge buffer with p^_i; one thread per team combines them, row by row
+    // in the same order and arithmetic as a per-row team sum, at the next flush (where the CTA
+    // synchronises anyway) instead of a team barrier on every row.
+    constexpr int HALF = (NTEAMS + 1) / 2;  // rows of Jp floats in the merge buffer
+    const int wrows = every * S.rpt;        // rows a team sees between two flushes
+    const bool defer = TW > 1 && (int64_t)wrows * NTEAMS * (2 * TW + 1) <= (int64_t)HALF * Jp;
+    float2* wpair = reinterpret_cast<float2*>(comb);                       // [NTEAMS][wrows][TW]
+    float* wph = comb + 2 * (size_t)NTEAMS * wrows * TW;                   // [NTEAMS][wrows]
+    int wr = 0;
     const int* pend = sh->pend - v0;
     int vp = v0, vbeg = 0;
     int vend = v0 < v1 ? pend[v0] : 0;
@@ -562,14 +572,35 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
                             if (col + c < J) P.pi[i * P.pi_ld + col + c] = pf * comp(x, c);
                 }
             }
-            const float2 r = team_sum_pair<TW>(rsum, sh->red, NTEAMS, tm, par);
-            errt = fmaf(phat, fabsf((r.x - 1.0f) + r.y), errt);
+            if (defer) {
+                float e = 0.f;
+                warp_sum_pair(rsum, e);
+                if (tm.lane == 0) wpair[((size_t)tm.team * wrows + wr) * TW + tm.wit] = make_float2(rsum, e);
+                if (tm.tl == 0) wph[tm.team * wrows + wr] = phat;
+                ++wr;
+            } else {
+                const float2 r = team_sum_pair<TW>(rsum, sh->red, NTEAMS, tm, par);
+                errt = fmaf(phat, fabsf((r.x - 1.0f) + r.y), errt);
+            }
         }
         __syncwarp();
         if (!EUC && lane == 0) mbar_arrive(&empty[st]);
         ++cseq;
         const bool at_end = (kb + 1 == vend);
         if ((kb + 1 - vbeg) % every == 0 || at_end) {
+            if (defer) {
+                bar_named(CONS_BAR, NC);  // every warp's parked row pairs are visible
+                if (tm.tl == 0)
+                    for (int k = 0; k < wr; ++k) {
+                        const float2* r = wpair + ((size_t)tm.team * wrows + k) * TW;
+                        float2 a = r[0];
+#pragma unroll
+                        for (int w = 1; w < TW; ++w) a = df_add2(a, r[w]);
+                        errt = fmaf(wph[tm.team * wrows + k], fabsf((a.x - 1.0f) + a.y), errt);
+                    }
+                wr = 0;
+                bar_named(CONS_BAR, NC);  // the merge buffer is free for the column sums
+            }
             // Reductions without a returned value: the thread that zeroed fp[j] is the one that
             // adds to it, flush after flush, so the sums are the serial ones, bit for bit, but no
             // thread waits on L2 for the old value (at 4,096 columns a read-modify-write per
