@@ -601,13 +601,21 @@ __device__ __forceinline__ void sk_finalize_sweep(const SolveParams& P, const St
                 wr = 0;
                 bar_named(CONS_BAR, NC);  // the merge buffer is free for the column sums
             }
-            // Reductions without a returned value: the thread that zeroed fp[j] is the one that
-            // adds to it, flush after flush, so the sums are the serial ones, bit for bit, but no
-            // thread waits on L2 for the old value (at 4,096 columns a read-modify-write per
-            // column made the flushes cost as much as the sweep).
+            // Wide rows (multi-warp teams): reductions without a returned value.  The thread that
+            // zeroed fp[j] is the one that adds to it, flush after flush, so the sums are the
+            // serial ones, bit for bit, but no thread waits on L2 for the old value (at 4,096
+            // columns a read-modify-write per column cost 0.2 ms of a 2.2 ms finalize).  One-warp
+            // teams keep the read-modify-write: there the flushes are rare, and the reductions
+            // changed the register allocation of the whole solver loop (1.5% slower at 800
+            // columns).
             double2* fp = P.fpart + (int64_t)vp * Jp;
-            cta_col_sum<TW, VPT>(comb, cpi, J, Jp, tm, [&](int j, float sum) { atomicAdd(&fp[j].x, (double)sum); });
-            cta_col_sum<TW, VPT>(comb, crho, J, Jp, tm, [&](int j, float sum) { atomicAdd(&fp[j].y, (double)sum); });
+            if constexpr (TW > 1) {
+                cta_col_sum<TW, VPT>(comb, cpi, J, Jp, tm, [&](int j, float sum) { atomicAdd(&fp[j].x, (double)sum); });
+                cta_col_sum<TW, VPT>(comb, crho, J, Jp, tm, [&](int j, float sum) { atomicAdd(&fp[j].y, (double)sum); });
+            } else {
+                cta_col_sum<TW, VPT>(comb, cpi, J, Jp, tm, [&](int j, float sum) { fp[j].x += (double)sum; });
+                cta_col_sum<TW, VPT>(comb, crho, J, Jp, tm, [&](int j, float sum) { fp[j].y += (double)sum; });
+            }
 #pragma unroll
             for (int v = 0; v < VPT; ++v) cpi[v] = crho[v] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
