@@ -215,7 +215,7 @@ template <typename T, int TW, int VPT, bool RR, int NCW>
 __device__ __forceinline__ bool lp_consumers(const LpParams& P, const StreamCfg& S, GroupCtx& g, SkShared* sh,
                                              unsigned char* dyn, int64_t r0, int64_t r1) {
     constexpr int N = Chunk<T>::N;
-    static_assert(NCW <= 24 && NCW / TW <= 12 && 2 * (NCW / TW) * TW <= 64, "SkShared sizes");
+    static_assert(NCW <= 24 && NCW / TW <= 16 && 2 * (NCW / TW) * TW <= 64, "SkShared sizes");
     constexpr int TT = 32 * TW, NTEAMS = NCW / TW, NC = NCW * 32;
     uint64_t* full = reinterpret_cast<uint64_t*>(dyn);
     uint64_t* empty = full + MAX_STAGES;
