@@ -120,12 +120,12 @@ static inline void split_k(double k, float* hi, float* lo) {
 // busiest sub-partition runs 4 warps gets 128 registers a thread, whether the block has 13
 // warps or 16.  One-warp teams take the full 16 (15 consumers + the producer): the sweep is
 // latency-bound, and 15 warps instead of 12 at the same 128 registers made the 50,000 x 800
-// solves 10% faster.  Teams of 2 and 4 warps keep 12 consumers (a multiple of the team
-// width that still fits 4 warps a sub-partition with the producer); 8 when a row needs a
-// team of 8 warps.
+// solves 10% faster.  Other team widths take the largest multiple of the width that still
+// fits: 14 for teams of 2 (5% faster than 12 at 200,000 x 1,536), 12 for teams of 4, and 8
+// when a row needs a team of 8 warps.
 template <int TW>
 struct Cons {
-    static constexpr int NCW = (TW == 8) ? 8 : (TW == 1 ? 15 : 12);
+    static constexpr int NCW = (TW == 8) ? 8 : (TW == 1 ? 15 : (TW == 2 ? 14 : 12));
     static constexpr int NT = 32 * (NCW + 1);  // + one producer warp
 };
 static constexpr int MAX_STAGES = 8;
