@@ -12,7 +12,10 @@
 // published request from a queue in host-mapped memory (the host appends while the kernel
 // runs), solves and finalizes it (the batched solver's group code), writes the result to
 // host-mapped memory and takes the next.  A group that finds no work for `idle` polls
-// leaves; when all have left the launch ends and the host starts a new one when work comes.
+// counts itself idle; when every group is counted, the launch closes (one compare-and-swap
+// marks the count) and all groups leave together; the host starts a new launch when work
+// comes.  A counted group leaves the count before it claims work, which a closing launch
+// refuses: a launch never goes on with only some of its groups.
 // A request's result depends only on its cell's data (row partitions fix every reduction
 // order), so it is the same alone and in any mix.  Every wait is bounded.
 #include <cuda_runtime.h>
@@ -59,8 +62,10 @@ struct SvQueue {
 struct SvCtl {  // device memory, zeroed once
     unsigned head;  // descriptors claimed
     int abort;
-    unsigned idle;  // groups of the current launch that found no work (zeroed per launch)
+    unsigned idle;  // groups of the current launch that found no work, | SV_CLOSING once every
+                    // group was counted and the launch is ending (zeroed per launch)
 };
+constexpr unsigned SV_CLOSING = 1u << 31;
 
 struct ServeParams {
     SvQueue* q;          // device view of the mapped queue
@@ -239,19 +244,29 @@ __global__ void __launch_bounds__(BT_NT, 1) sk_serve(ServeParams S) {
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) {
             // claim the next published request.  A group that found nothing for idle_polls
-            // polls reports itself idle and keeps polling; when every group of the launch is
-            // idle they all leave (the host relaunches on new work).  At most `spin` polls.
+            // polls counts itself idle and keeps polling.  The group that finds every group
+            // counted closes the launch (CAS: all counted -> all counted | CLOSING) and every
+            // group leaves; a counted group that sees work first leaves the count, by a CAS
+            // that fails once the launch is closing.  So either all groups stay or all leave
+            // (the host relaunches on new work).  At most `spin` polls.
             int idx = -1;
             long long n = 0;
             bool counted = false;
+            const unsigned all = (unsigned)S.ngroups;
             for (;;) {
                 if (ld_acquire_sys_u32(&S.q->stop)) break;
+                const unsigned iv = *(volatile unsigned*)&S.ctl->idle;
+                if (iv & SV_CLOSING) break;
                 const unsigned t = ld_acquire_sys_u32(&S.q->tail);
                 const unsigned h = *(volatile unsigned*)&S.ctl->head;
                 if (h < t) {
+                    if (counted) {
+                        if (atomicCAS(&S.ctl->idle, iv, iv - 1u) != iv) continue;  // changed: look again
+                        counted = false;
+                        n = 0;
+                    }
                     if (atomicCAS(&S.ctl->head, h, h + 1) == h) {
                         idx = (int)h;
-                        if (counted) atomicSub(&S.ctl->idle, 1u);
                         break;
                     }
                     continue;
@@ -260,8 +275,9 @@ __global__ void __launch_bounds__(BT_NT, 1) sk_serve(ServeParams S) {
                 if (!counted && n > S.idle_polls) {
                     atomicAdd(&S.ctl->idle, 1u);
                     counted = true;
+                    continue;
                 }
-                if (counted && *(volatile unsigned*)&S.ctl->idle >= (unsigned)S.ngroups) break;
+                if (counted && iv == all && atomicCAS(&S.ctl->idle, all, all | SV_CLOSING) == all) break;
                 if (n > S.spin) break;
                 __nanosleep(n < 4096 ? 256 : 2048);
             }
