@@ -478,6 +478,81 @@ ot_status ot_assoc_solve_eps_scaling(ot_assoc_ctx* ctx, const float* C, int64_t 
                                      int32_t* nstages_out, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Row-sharded Algorithm 1 (Sec. III-C, Eqs. (3)-(5)): the rows of C split into contiguous
+ * shards (one per rank / GPU).  The row update (Eq. (3)) only needs a shard's own rows; the
+ * column update (Eq. (4)) needs the column sums of every shard, so one iteration is
+ *   ot_assoc_shard_sweep(ITER)   on every shard,
+ *   a SUM over the shards of col_out (J doubles) and row_out (1 double)  [the caller's
+ *   collective, e.g. an all-reduce],
+ *   ot_assoc_shard_update(ITER)  on every rank (same inputs, same G).
+ * The cell, the stopping rule and the outputs are those of ot_assoc_solve_cost; a driver
+ * that strings the calls together is paper_1805_01559_gb300.sharded.  Common arguments:
+ *   C        [device] float I x J, this shard's rows; 16-byte aligned, ld_c % 4 == 0 (0 = J)
+ *   p        [device] float I, this shard's row marginals (> 0)
+ *   inv_mass = 1 / (sum of p over ALL shards) (host), so p^_i = p_i * inv_mass
+ *   eps      > 0 (absolute); k = log2(e) / eps
+ *   G        [device] double J: column potentials in log2 units (g_j = eps ln2 G_j)
+ *   F_in, F_out [device] float 2 I: row potentials F'_i as (hi, lo) FP32 pairs, row-relative
+ *            log2 units: t_ij = 2^(F'_i + G_j - k C_ij) = pi_ij / p_i
+ * Modes of the sweep (outputs summed over the shards unless said otherwise):
+ *   OT_SHARD_FIRST  iteration 1 from G: F_out = F'^1 = -log2 sum_j 2^(G_j - k C_ij);
+ *                   col_out[j] = 2^64 sum_i p^_i 2^(F'^1_i + G_j - k C_ij)
+ *   OT_SHARD_ITER   F_in = F'^(k-1): F_out = F'^k (Eq. (3)); col_out[j] = s_j =
+ *                   sum_i p^_i 2^(F'^k_i + G_j - k C_ij); row_out = sum_i p^_i |r_i - 1|,
+ *                   r_i = sum_j t_ij: the row residual of the plan (F'^(k-1), G)
+ *   OT_SHARD_COLMAX col_out[j] = max_i (F_in_i + G_j - k C_ij + log2 p^_i)  (reduce with MAX)
+ *   OT_SHARD_COLSUM col_out[j] = sum_i 2^(F_in_i + G_j - k C_ij + log2 p^_i - M_j), M = colmax
+ *                   (the reduced COLMAX output): COLMAX then COLSUM take iteration 1's
+ *                   column sums exactly when FIRST's scaled sums underflow
+ *   OT_SHARD_FINAL  plan (F_in, G): col_out[0..J) = sum_i p^_i t_ij, col_out[J..2J) =
+ *                   sum_i p^_i C_ij t_ij; row_out = sum_i p^_i |r_i - 1| (FP32 pair row sums);
+ *                   f_out [device] double I (this shard) = eps ln2 (F'_i + log2 p_i), or NULL
+ * col_out [device] double J (2 J for FINAL); row_out [device] double 1 (ITER, FINAL).
+ * Per-block FP64 partials added in block order: deterministic for a given shard and device.
+ * Uses the context's scratch: issue a context's shard calls on one stream.  Only enqueues.
+ * OT_EUNSUPPORTED for J > 8192; OT_EINVAL for a misaligned C or a missing buffer.
+ * ------------------------------------------------------------------------------------- */
+enum {
+    OT_SHARD_FIRST = 0,
+    OT_SHARD_ITER = 1,
+    OT_SHARD_COLMAX = 2,
+    OT_SHARD_COLSUM = 3,
+    OT_SHARD_FINAL = 4
+};
+
+/* out [device] double 3: sum of this shard's p, sum of q, and 1.0 when an entry of p or q is
+ * not positive and finite (else 0.0).  Fixed summation order.  Only enqueues. */
+ot_status ot_assoc_shard_mass(ot_assoc_ctx* ctx, const float* p, int64_t I, const float* q, int64_t J,
+                              double* out, void* stream);
+
+ot_status ot_assoc_shard_sweep(ot_assoc_ctx* ctx, int mode, const float* C, int64_t ld_c, const float* p,
+                               int64_t I, int64_t J, double inv_mass, double eps, const double* G,
+                               const float* F_in, float* F_out, const double* colmax, double* col_out,
+                               double* row_out, double* f_out, void* stream);
+
+/* Column update (Eq. (4)) from the summed col of every shard, q [device] float J,
+ * inv_qmass = 1 / sum q:
+ *   FIRST   G_out = G_in + log2 q^ - (log2 col - 64); a column whose scaled sum is below 2^-60
+ *           (or not finite) sets bit 1 of *flag and leaves its G_out entry unset: take
+ *           iteration 1 again with COLMAX / COLSUM (G_in is unchanged when G_out differs)
+ *   COLSUM  G_out = G_in + log2 q^ - (M + log2 col), M = colmax as the sweep rounded it
+ *   ITER    G_out = G_in + log2 q^ - log2 col
+ * A sum that is not positive and finite sets bit 2 of *flag (numeric failure).  flag
+ * [device] int32, only ever OR-ed: the caller zeroes it.  G_out may equal G_in.  Only enqueues. */
+ot_status ot_assoc_shard_update(ot_assoc_ctx* ctx, int mode, const float* q, int64_t J, double inv_qmass,
+                                const double* col, const double* colmax, const double* G_in, double* G_out,
+                                int32_t* flag, void* stream);
+
+/* Totals of the FINAL sweep from the summed col2 (2 J) and row_err (1): summary [device]
+ * double 3 = transport cost (mass * sum_j col2[J + j]), row residual, column residual
+ * sum_j |col2[j] - q_j inv_qmass|; rho_out [device] double J (mass * col2[J + j]) or NULL;
+ * g_out [device] double J = eps ln2 G, or NULL.  mass = sum of p over all shards.  Only
+ * enqueues. */
+ot_status ot_assoc_shard_finish(ot_assoc_ctx* ctx, const double* col2, const double* row_err, const float* q,
+                                int64_t J, double mass, double inv_qmass, double eps, const double* G,
+                                double* g_out, double* rho_out, double* summary, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Adaptive Sinkhorn association (Algorithm 2, Sec. V) in ONE persistent launch.
  * The RRH targets start from the equal split q_j = sum_i lambda_i / J (Algorithm 2,
  * initialisation).  Each outer step s:

@@ -1065,3 +1065,67 @@ def _ctx_build_cost_mobile(self, dev_xy, dev_v, rrh_xy, shadow_db, P, dt, side_m
 
 
 Context.build_cost_mobile = _ctx_build_cost_mobile
+
+
+# ---- row-sharded Algorithm 1 (Sec. III-C): the steps of one iteration over a shard ----------
+OT_SHARD_FIRST, OT_SHARD_ITER, OT_SHARD_COLMAX, OT_SHARD_COLSUM, OT_SHARD_FINAL = 0, 1, 2, 3, 4
+_CI = ctypes.c_int
+SIGNATURES["ot_assoc_shard_mass"] = (ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _VP, _VP])
+SIGNATURES["ot_assoc_shard_sweep"] = (ctypes.c_int, [_VP, _CI, _VP, _I64, _VP, _I64, _I64, _D, _D, _VP, _VP, _VP,
+                                                     _VP, _VP, _VP, _VP, _VP])
+SIGNATURES["ot_assoc_shard_update"] = (ctypes.c_int, [_VP, _CI, _VP, _I64, _D, _VP, _VP, _VP, _VP, _VP, _VP])
+SIGNATURES["ot_assoc_shard_finish"] = (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _D, _D, _D, _VP, _VP, _VP, _VP,
+                                                      _VP])
+if _lib is not None:
+    for _name in ("ot_assoc_shard_mass", "ot_assoc_shard_sweep", "ot_assoc_shard_update", "ot_assoc_shard_finish"):
+        _fn = getattr(_lib, _name)
+        _fn.restype, _fn.argtypes = SIGNATURES[_name]
+
+
+def _ctx_shard_mass(self, p, q, out, stream=None) -> None:
+    """out (3 doubles) = sum of p, sum of q, 1.0 when an entry is not positive and finite."""
+    _need(p, torch.float32, "p", 1)
+    _need(q, torch.float32, "q", 1)
+    _need(out, torch.float64, "out", 1)
+    self._check(self._L.ot_assoc_shard_mass(self._h, _ptr(p), p.numel(), _ptr(q), q.numel(), _ptr(out),
+                                            _stream(stream)))
+
+
+def _ctx_shard_sweep(self, mode, C, p, inv_mass, eps, G, F_in, F_out, colmax, col_out, row_out=None, f_out=None,
+                     stream=None) -> None:
+    """One sweep of Algorithm 1 over a shard's rows (mode OT_SHARD_*); F_in / F_out are float32
+    (I, 2) row-potential pairs; every output is a caller tensor."""
+    _need(C, torch.float32, "C", 2)
+    _need(p, torch.float32, "p", 1)
+    _need(G, torch.float64, "G", 1)
+    _need(col_out, torch.float64, "col_out", 1)
+    for name, t in (("F_in", F_in), ("F_out", F_out)):
+        if t is not None:
+            _need(t, torch.float32, name, 2)
+    I, J = C.shape
+    self._check(self._L.ot_assoc_shard_sweep(
+        self._h, int(mode), _ptr(C), C.stride(0), _ptr(p), I, J, float(inv_mass), float(eps), _ptr(G), _ptr(F_in),
+        _ptr(F_out), _ptr(colmax), _ptr(col_out), _ptr(row_out), _ptr(f_out), _stream(stream)))
+
+
+def _ctx_shard_update(self, mode, q, inv_qmass, col, colmax, G_in, G_out, flag, stream=None) -> None:
+    """Column update from the column sums of every shard; flag (int32, 1) is OR-ed on trouble."""
+    _need(q, torch.float32, "q", 1)
+    _need(flag, torch.int32, "flag", 1)
+    self._check(self._L.ot_assoc_shard_update(self._h, int(mode), _ptr(q), q.numel(), float(inv_qmass), _ptr(col),
+                                              _ptr(colmax), _ptr(G_in), _ptr(G_out), _ptr(flag), _stream(stream)))
+
+
+def _ctx_shard_finish(self, col2, row_err, q, mass, inv_qmass, eps, G, g_out, rho_out, summary, stream=None) -> None:
+    """Totals of the finalize sweep: summary = (transport cost, row residual, column residual)."""
+    _need(q, torch.float32, "q", 1)
+    _need(summary, torch.float64, "summary", 1)
+    self._check(self._L.ot_assoc_shard_finish(self._h, _ptr(col2), _ptr(row_err), _ptr(q), q.numel(), float(mass),
+                                              float(inv_qmass), float(eps), _ptr(G), _ptr(g_out), _ptr(rho_out),
+                                              _ptr(summary), _stream(stream)))
+
+
+Context.shard_mass = _ctx_shard_mass
+Context.shard_sweep = _ctx_shard_sweep
+Context.shard_update = _ctx_shard_update
+Context.shard_finish = _ctx_shard_finish

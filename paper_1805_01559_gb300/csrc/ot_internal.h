@@ -28,6 +28,7 @@ enum ScratchSlot {
     SLOT_SCAL,         // scaling vectors u, v, drift references (low precision form)
     SLOT_ALIGN,        // 16-byte-aligned copies of unaligned caller inputs (G, R)
     SLOT_TUNE,         // autotuner outputs (potentials of the timed runs)
+    SLOT_SHARD,        // row-sharded sweeps: per-block column partials
     SLOT_COUNT
 };
 
