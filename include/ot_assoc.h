@@ -625,7 +625,7 @@ ot_status ot_assoc_adaptive(ot_assoc_ctx* ctx, const float* C, int64_t ld_c, con
 typedef struct ot_assoc_server ot_assoc_server;
 
 typedef struct {
-    int32_t group_ctas;  /* CTAs per group (divides the SM count); 0 = 8 */
+    int32_t group_ctas;  /* CTAs per group (divides the SM count); 0 = a quarter of the SMs */
     int32_t max_J;       /* largest J of any cell (group scratch); 0 = 1024 */
     double idle_us;      /* a group with no work waits this long before the launch may end; 0 = 200 */
     size_t hbm_budget;   /* bytes of resident cell state; 0 = no limit */

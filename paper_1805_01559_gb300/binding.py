@@ -624,7 +624,7 @@ class ServerResult:
 class Server:
     """ot_assoc_server: resident cells, continuously batched warm-started solves."""
 
-    def __init__(self, ctx: "Context", group_ctas: int = 8, max_J: int = 1024, idle_us: float = 200.0,
+    def __init__(self, ctx: "Context", group_ctas: int = 0, max_J: int = 1024, idle_us: float = 200.0,
                  hbm_budget: int = 0):
         self._ctx = ctx
         self._L = ctx._L

@@ -636,7 +636,10 @@ ot_status ot_assoc_server_create(ot_assoc_ctx* ctx, const ot_assoc_server_config
     s->ctx = ctx;
     if (cfg) s->cfg = *cfg;
     const int nsm = ctx->num_sms;
-    s->gsize = s->cfg.group_ctas > 0 ? s->cfg.group_ctas : 8;
+    // default: four groups (a quarter of the SMs each), the best measured on the mixed-size
+    // serving cells (groups of 152 / 76 / 38 / 19 CTAs served 1298 / 1658 / 2838 / 2821
+    // solves/s on 152 SMs); an SM count that is not a multiple of 4 takes one group
+    s->gsize = s->cfg.group_ctas > 0 ? s->cfg.group_ctas : (nsm % 4 == 0 ? nsm / 4 : nsm);
     if (nsm % s->gsize != 0) {
         delete s;
         return set_error(ctx, OT_EINVAL, "group_ctas must divide the SM count (%d)", nsm);
