@@ -1210,6 +1210,75 @@ def run_euclid(args):
     return 0
 
 
+def run_sharded(args):
+    """The row-sharded form of Algorithm 1 (ot_assoc_shard_*, sharded.solve_sharded) on the
+    50,000 x 800 step's instance at eps = {0.1, 0.03, 0.01} x median(C): the rows split into
+    --shards blocks, emulated in this process on the one GPU (each shard its own launches, the
+    sum over the shards formed between launches), against the single-GPU persistent solve.
+    One rank of a multi-GPU run does the work of one shard plus one all-reduce of J + 1
+    doubles per iteration; here every shard runs on the same GPU, one after the other."""
+    import torch
+
+    from paper_1805_01559_gb300 import binding, sharded as S
+    inst = make_inputs()
+    I, J = inst.I, inst.J
+    dev = torch.device("cuda", 0)
+    ctx = binding.Context(0)
+    G = torch.from_numpy(np.ascontiguousarray(inst.G, np.float32)).to(dev)
+    P = torch.from_numpy(inst.P.astype(np.float32)).to(dev)
+    lam = torch.from_numpy(inst.lam.astype(np.float32)).to(dev)
+    q = torch.from_numpy(inst.q.astype(np.float32)).to(dev)
+    C, med = ctx.build_cost_from_gains(G, P, inst.N0, inst.W_hz, inst.mu, eps_rel=1.0)
+    cuts = [round(I * k / args.shards) for k in range(args.shards + 1)]
+    shards = [(C[cuts[k]:cuts[k + 1]], lam[cuts[k]:cuts[k + 1]]) for k in range(args.shards)]
+    ops = S.DeviceOps(ctx)
+    s = torch.cuda.current_stream()
+
+    def sharded():
+        return [S.solve_sharded(ops, shards, q, er * med, tol=TOL, max_iter=MAX_ITER).iters for er in EPS_REL]
+
+    def single():
+        return [ctx.solve_cost(C, lam, q, er * med, tol=TOL, max_iter=MAX_ITER).iters for er in EPS_REL]
+
+    for _ in range(args.warmup):
+        sharded()
+        single()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = ctx.launch_count()
+    ms_s, its = [], None
+    for _ in range(args.steps):
+        its, ms, _ = _timed(sharded, s)
+        ms_s.append(ms)
+    launches = (ctx.launch_count() - l0) / args.steps
+    clk = clocks.stop()
+    ms_1, its_1 = [], None
+    for _ in range(args.steps):
+        its_1, ms, _ = _timed(single, s)
+        ms_1.append(ms)
+    ms, ms1 = statistics.median(ms_s), statistics.median(ms_1)
+    ci = float(I) * J * sum(its)
+    peak, peak_kind = _peaks()
+    # every iteration reads C once, plus iteration 1's and the finalize's reads
+    sweeps = sum(it + 2 for it in its)
+    achieved = 4.0 * I * J * sweeps / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": ci / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"sharded_50000x800: rows in {args.shards} shards on one GPU, "
+                                   "eps = {0.1,0.03,0.01} x median(C)", "I": I, "J": J, "shards": args.shards,
+                       "iters": its, "tol": TOL, "l2": "inputs larger than L2 (C 160 MB)"},
+            "single_gpu_solve": {"ms": ms1, "iters": its_1, "cells_iters_per_s": float(I) * J * sum(its_1) / (ms1 / 1e3)},
+            "roofline": {"bound": "hbm", "kernel": "k_shard_sweep (+ k_shard_reduce, k_shard_update per iteration)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_kind": peak_kind,
+                         "definition": "4 B x I x J x (iters + 2) over the call (every sweep reads C once)"},
+            "gpu_launches": launches, "clocks": clk}
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_epsscale(args):
     """eps-scaling on the 50,000 x 800 step's instance: Algorithm 1 at eps = e x median(C)
     from b = 1 (sk_solve) against the same eps reached through the stages 0.1 -> 0.03 -> ...
@@ -1292,7 +1361,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=12_500)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="only run this many rounds of the three solves of one step (for profiler captures)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2", "policies", "euclid", "epsscale"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2", "policies", "euclid", "epsscale", "sharded"],
                     help="c2: the headline line; c3 batched ragged; c4 stored-kernel precision; c5 serving; "
                          "alg2 adaptive association (Algorithm 2)")
     ap.add_argument("--alg2-outer", type=int, default=20)
@@ -1300,6 +1369,7 @@ def main():
     ap.add_argument("--c3-instances", type=int, default=256)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--c4-rows", type=int, default=400_000)
+    ap.add_argument("--shards", type=int, default=2, help="sharded workload: row blocks on the one GPU")
     ap.add_argument("--c5-rate", type=float, default=2000.0)
     ap.add_argument("--c5-seconds", type=float, default=10.0)
     ap.add_argument("--c5-group", type=int, default=38)
@@ -1315,7 +1385,8 @@ def main():
         return run_profile_solve(args)
     if args.workload != "c2" and args.impl != "reference":
         return {"c3": run_c3, "c4": run_c4, "c5": run_c5, "alg2": run_alg2,
-                "policies": run_policies, "euclid": run_euclid, "epsscale": run_epsscale}[args.workload](args)
+                "policies": run_policies, "euclid": run_euclid, "epsscale": run_epsscale,
+                "sharded": run_sharded}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
