@@ -508,6 +508,8 @@ ot_status ot_assoc_solve_eps_scaling(ot_assoc_ctx* ctx, const float* C, int64_t 
  *                   sum_i p^_i C_ij t_ij; row_out = sum_i p^_i |r_i - 1| (FP32 pair row sums);
  *                   f_out [device] double I (this shard) = eps ln2 (F'_i + log2 p_i), or NULL
  * col_out [device] double J (2 J for FINAL); row_out [device] double 1 (ITER, FINAL).
+ * state [device] double 4 or NULL: the loop state of ot_assoc_shard_update; while state[0]
+ * is not 0 the sweep does nothing (so a caller can enqueue iterations ahead of the stop).
  * Per-block FP64 partials added in block order: deterministic for a given shard and device.
  * Uses the context's scratch: issue a context's shard calls on one stream.  Only enqueues.
  * OT_EUNSUPPORTED for J > 8192; OT_EINVAL for a misaligned C or a missing buffer.
@@ -528,7 +530,7 @@ ot_status ot_assoc_shard_mass(ot_assoc_ctx* ctx, const float* p, int64_t I, cons
 ot_status ot_assoc_shard_sweep(ot_assoc_ctx* ctx, int mode, const float* C, int64_t ld_c, const float* p,
                                int64_t I, int64_t J, double inv_mass, double eps, const double* G,
                                const float* F_in, float* F_out, const double* colmax, double* col_out,
-                               double* row_out, double* f_out, void* stream);
+                               double* row_out, double* f_out, const double* state, void* stream);
 
 /* Column update (Eq. (4)) from the summed col of every shard, q [device] float J,
  * inv_qmass = 1 / sum q:
@@ -538,10 +540,19 @@ ot_status ot_assoc_shard_sweep(ot_assoc_ctx* ctx, int mode, const float* C, int6
  *   COLSUM  G_out = G_in + log2 q^ - (M + log2 col), M = colmax as the sweep rounded it
  *   ITER    G_out = G_in + log2 q^ - log2 col
  * A sum that is not positive and finite sets bit 2 of *flag (numeric failure).  flag
- * [device] int32, only ever OR-ed: the caller zeroes it.  G_out may equal G_in.  Only enqueues. */
+ * [device] int32, only ever OR-ed: the caller zeroes it.  G_out may equal G_in.
+ * Loop state (ITER with state [device] double 4, zeroed by the caller before the loop; else
+ * NULL and err, iter, tol_stop, max_iter unused): the update first takes the loop test of
+ * Algorithm 1 on the summed row residual *err [device] (of the plan (F'^(iter-1), G_in)):
+ * when err <= tol_stop or iter - 1 >= max_iter (or err is not finite) it leaves G as it is and
+ * sets state = {reason, iter - 1, (iter - 1) & 1, err}, reason 1 = converged, 2 = max_iter,
+ * 3 = numeric failure (also set when a column sum fails); (iter - 1) & 1 is the F buffer of the
+ * returned plan when F'^k is written to buffer k & 1.  Every update and sweep that sees
+ * state[0] != 0 does nothing.  Only enqueues. */
 ot_status ot_assoc_shard_update(ot_assoc_ctx* ctx, int mode, const float* q, int64_t J, double inv_qmass,
                                 const double* col, const double* colmax, const double* G_in, double* G_out,
-                                int32_t* flag, void* stream);
+                                int32_t* flag, const double* err, int32_t iter, double tol_stop,
+                                int32_t max_iter, double* state, void* stream);
 
 /* Totals of the FINAL sweep from the summed col2 (2 J) and row_err (1): summary [device]
  * double 3 = transport cost (mass * sum_j col2[J + j]), row residual, column residual

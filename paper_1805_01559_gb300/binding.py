@@ -1072,8 +1072,9 @@ OT_SHARD_FIRST, OT_SHARD_ITER, OT_SHARD_COLMAX, OT_SHARD_COLSUM, OT_SHARD_FINAL 
 _CI = ctypes.c_int
 SIGNATURES["ot_assoc_shard_mass"] = (ctypes.c_int, [_VP, _VP, _I64, _VP, _I64, _VP, _VP])
 SIGNATURES["ot_assoc_shard_sweep"] = (ctypes.c_int, [_VP, _CI, _VP, _I64, _VP, _I64, _I64, _D, _D, _VP, _VP, _VP,
-                                                     _VP, _VP, _VP, _VP, _VP])
-SIGNATURES["ot_assoc_shard_update"] = (ctypes.c_int, [_VP, _CI, _VP, _I64, _D, _VP, _VP, _VP, _VP, _VP, _VP])
+                                                     _VP, _VP, _VP, _VP, _VP, _VP])
+SIGNATURES["ot_assoc_shard_update"] = (ctypes.c_int, [_VP, _CI, _VP, _I64, _D, _VP, _VP, _VP, _VP, _VP, _VP, _I32,
+                                                      _D, _I32, _VP, _VP])
 SIGNATURES["ot_assoc_shard_finish"] = (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _D, _D, _D, _VP, _VP, _VP, _VP,
                                                       _VP])
 if _lib is not None:
@@ -1092,9 +1093,10 @@ def _ctx_shard_mass(self, p, q, out, stream=None) -> None:
 
 
 def _ctx_shard_sweep(self, mode, C, p, inv_mass, eps, G, F_in, F_out, colmax, col_out, row_out=None, f_out=None,
-                     stream=None) -> None:
+                     state=None, stream=None) -> None:
     """One sweep of Algorithm 1 over a shard's rows (mode OT_SHARD_*); F_in / F_out are float32
-    (I, 2) row-potential pairs; every output is a caller tensor."""
+    (I, 2) row-potential pairs; every output is a caller tensor; with a loop state (float64, 4)
+    the sweep does nothing once the loop has stopped."""
     _need(C, torch.float32, "C", 2)
     _need(p, torch.float32, "p", 1)
     _need(G, torch.float64, "G", 1)
@@ -1105,15 +1107,18 @@ def _ctx_shard_sweep(self, mode, C, p, inv_mass, eps, G, F_in, F_out, colmax, co
     I, J = C.shape
     self._check(self._L.ot_assoc_shard_sweep(
         self._h, int(mode), _ptr(C), C.stride(0), _ptr(p), I, J, float(inv_mass), float(eps), _ptr(G), _ptr(F_in),
-        _ptr(F_out), _ptr(colmax), _ptr(col_out), _ptr(row_out), _ptr(f_out), _stream(stream)))
+        _ptr(F_out), _ptr(colmax), _ptr(col_out), _ptr(row_out), _ptr(f_out), _ptr(state), _stream(stream)))
 
 
-def _ctx_shard_update(self, mode, q, inv_qmass, col, colmax, G_in, G_out, flag, stream=None) -> None:
-    """Column update from the column sums of every shard; flag (int32, 1) is OR-ed on trouble."""
+def _ctx_shard_update(self, mode, q, inv_qmass, col, colmax, G_in, G_out, flag, err=None, it=0, tol_stop=0.0,
+                      max_iter=0, state=None, stream=None) -> None:
+    """Column update from the column sums of every shard; flag (int32, 1) is OR-ed on trouble.
+    With a loop state (ITER): the loop test on the summed residual err first (see the header)."""
     _need(q, torch.float32, "q", 1)
     _need(flag, torch.int32, "flag", 1)
     self._check(self._L.ot_assoc_shard_update(self._h, int(mode), _ptr(q), q.numel(), float(inv_qmass), _ptr(col),
-                                              _ptr(colmax), _ptr(G_in), _ptr(G_out), _ptr(flag), _stream(stream)))
+                                              _ptr(colmax), _ptr(G_in), _ptr(G_out), _ptr(flag), _ptr(err), int(it),
+                                              float(tol_stop), int(max_iter), _ptr(state), _stream(stream)))
 
 
 def _ctx_shard_finish(self, col2, row_err, q, mass, inv_qmass, eps, G, g_out, rho_out, summary, stream=None) -> None:

@@ -42,6 +42,7 @@ struct ShardArgs {
     double* part;          // [nb][NACC][Jp]
     double* epart;         // [nb]
     double* f_out;         // FINAL: natural-unit row potentials, or null
+    const double* state;   // loop state (state[0] != 0: the loop has stopped, do nothing), or null
 };
 
 template <int MODE>
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(SH_NW * 32) k_shard_sweep(ShardArgs a) {
     constexpr int NACC = ShardMode<MODE>::NACC;
     constexpr bool MAX = ShardMode<MODE>::MAX;
     extern __shared__ __align__(16) float shs[];
+    if (a.state && a.state[0] != 0.0) return;  // written only by earlier launches on the stream
     const int J = a.J, Jp = a.Jp;
     float* Gs = shs;              // [2 Jp]: hi, then lo
     float* Ms = shs + 2 * Jp;     // [Jp]
@@ -83,9 +85,15 @@ __global__ void __launch_bounds__(SH_NW * 32) k_shard_sweep(ShardArgs a) {
             acc[u][v] = make_float4(z, z, z, z);
         }
     float err = 0.f;  // this team's rows: sum of p^_i |r_i - 1|
-    for (int64_t i = (int64_t)blockIdx.x * NTEAMS + tm.team; i < a.I; i += (int64_t)gridDim.x * NTEAMS) {
+    const int64_t stride = (int64_t)gridDim.x * NTEAMS;
+    float4 xn[VPT];  // the team's next row, loaded while the current one is worked on
+    int64_t i = (int64_t)blockIdx.x * NTEAMS + tm.team;
+    if (i < a.I) load_row<TW, VPT>(a.C + i * a.ld, J, tm.tl, xn);  // columns >= J read as +inf
+    for (; i < a.I; i += stride) {
         float4 x[VPT];
-        load_row<TW, VPT>(a.C + i * a.ld, J, tm.tl, x);  // columns >= J read as +inf: no mass
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) x[v] = xn[v];
+        if (i + stride < a.I) load_row<TW, VPT>(a.C + (i + stride) * a.ld, J, tm.tl, xn);
         const float ph = __ldg(a.p + i) * a.inv_mass;     // p^_i
         if constexpr (MODE == OT_SHARD_FIRST) {
             // F'^1_i = -log2 sum_j 2^(G_j - k C_ij), shifted by the row's largest exponent
@@ -214,31 +222,76 @@ __global__ void __launch_bounds__(SH_NW * 32) k_shard_sweep(ShardArgs a) {
     }
 }
 
-// Columns (and the row residual) over the blocks, in block order.
-__global__ void k_shard_reduce(const double* __restrict__ part, const double* __restrict__ epart, int nb, int nacc,
-                               int Jp, int J, int is_max, double* col_out, double* row_out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < nacc * J) {
-        const int u = j / J, jj = j - u * J;
-        double s = is_max ? -INFINITY : 0.0;
-        for (int b = 0; b < nb; ++b) {
+// Columns (and the row residual) over the sweep's blocks.  A block of 32 warps takes 32
+// columns (one a lane); warp w adds the blocks w, w + 32, ... and the 32 warp sums are added
+// in warp order: a fixed order, so the result is deterministic.  Block 0 also adds the row
+// residuals (a fixed butterfly per warp, then the warps in order).
+constexpr int SR_WARPS = 32;
+__global__ void __launch_bounds__(SR_WARPS * 32) k_shard_reduce(const double* __restrict__ part,
+                                                                const double* __restrict__ epart, int nb, int nacc,
+                                                                int Jp, int J, int is_max, double* col_out,
+                                                                double* row_out, const double* state) {
+    __shared__ double sh[SR_WARPS][33];
+    if (state && state[0] != 0.0) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;  // column over the nacc accumulators
+    const bool in = j < nacc * J;
+    const int u = in ? j / J : 0, jj = in ? j - u * J : 0;
+    double s = is_max ? -INFINITY : 0.0;
+    if (in)
+        for (int b = w; b < nb; b += SR_WARPS) {
             const double y = part[((size_t)b * nacc + u) * Jp + jj];
             s = is_max ? fmax(s, y) : s + y;
         }
-        col_out[(size_t)u * J + jj] = s;
+    sh[w][lane] = s;
+    double e = 0.0;
+    if (row_out && blockIdx.x == 0) {
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) e += epart[b];
+        e = warp_sum(e);
     }
-    if (row_out && blockIdx.x == 0 && threadIdx.x == 0) {
-        double e = 0.0;
-        for (int b = 0; b < nb; ++b) e += epart[b];
-        *row_out = e;
+    __syncthreads();
+    if (w == 0 && in) {
+        double t = sh[0][lane];
+        for (int k = 1; k < SR_WARPS; ++k) t = is_max ? fmax(t, sh[k][lane]) : t + sh[k][lane];
+        col_out[(size_t)u * J + jj] = t;
+    }
+    if (row_out && blockIdx.x == 0) {
+        __syncthreads();
+        if (lane == 0) sh[w][32] = e;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < SR_WARPS; ++k) t += sh[k][32];
+            *row_out = t;
+        }
     }
 }
 
-// G^k_j = G^(k-1)_j + log2 q^_j - log2 s_j from the sums of every shard.
+// G^k_j = G^(k-1)_j + log2 q^_j - log2 s_j from the sums of every shard.  With a loop state
+// (ITER): the loop test on the reduced residual of the plan (F'^(k-1), G^(k-1)) first; on a
+// stop every thread leaves G as it is and thread 0 records iterations k - 1, the parity of the
+// row-potential buffer that holds F'^(k-1), the residual and the reason in the state.
 __global__ void k_shard_update(int mode, const float* __restrict__ q, int J, double inv_qmass,
                                const double* __restrict__ col, const double* __restrict__ colmax,
-                               const double* G_in, double* G_out, int* flag) {
+                               const double* G_in, double* G_out, int* flag, const double* err_in, int iter,
+                               double tol_stop, int max_iter, double* state) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (state) {
+        if (state[0] != 0.0) return;
+        if (mode == OT_SHARD_ITER) {
+            const double err = *err_in;  // every thread reads the same value: one decision
+            const bool conv = err <= tol_stop;
+            if (!isfinite(err) || conv || iter - 1 >= max_iter) {
+                if (j == 0) {
+                    state[1] = (double)(iter - 1);
+                    state[2] = (double)((iter - 1) & 1);
+                    state[3] = err;
+                    state[0] = !isfinite(err) ? 3.0 : (conv ? 1.0 : 2.0);
+                }
+                return;
+            }
+        }
+    }
     if (j >= J) return;
     const double lq = log2((double)q[j] * inv_qmass);
     const double c = col[j];
@@ -255,6 +308,7 @@ __global__ void k_shard_update(int mode, const float* __restrict__ q, int J, dou
         const double M = mode == OT_SHARD_COLSUM ? (double)(float)colmax[j] : 0.0;
         if (!(c > 0.0) || !isfinite(c) || !isfinite(M)) {
             atomicOr(flag, 2);
+            if (state) state[0] = 3.0;  // numeric failure: later launches do nothing
             return;
         }
         G_out[j] = G_in[j] + lq - (M + log2(c));
@@ -369,7 +423,7 @@ ot_status ot_assoc_shard_mass(ot_assoc_ctx* ctx, const float* p, int64_t I, cons
 ot_status ot_assoc_shard_sweep(ot_assoc_ctx* ctx, int mode, const float* C, int64_t ld_c, const float* p, int64_t I,
                                int64_t J, double inv_mass, double eps, const double* G, const float* F_in,
                                float* F_out, const double* colmax, double* col_out, double* row_out,
-                               double* f_out, void* stream) {
+                               double* f_out, const double* state, void* stream) {
     if (!ctx) return OT_EINVAL;
     DeviceGuardLite guard(ctx->device);
     if (mode < OT_SHARD_FIRST || mode > OT_SHARD_FINAL) return set_error(ctx, OT_EINVAL, "unknown shard mode %d", mode);
@@ -396,7 +450,9 @@ ot_status ot_assoc_shard_sweep(ot_assoc_ctx* ctx, int mode, const float* C, int6
                                : ShardKernels<8>::get(mode);
     const int Jp = (int)round_up(J, 4);
     const int nacc = mode == OT_SHARD_FINAL ? 2 : 1;
-    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((I + nteams - 1) / nteams, 4LL * ctx->num_sms));
+    // two blocks an SM (what fits at these register counts); every block adds its rows'
+    // column sums into one row of partials that k_shard_reduce then adds
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((I + nteams - 1) / nteams, 2LL * ctx->num_sms));
     const size_t smem = sizeof(float) * ((size_t)3 * Jp + (size_t)nteams * nacc * Jp);
     ot_status st = OT_OK;
     const size_t off_e = round_up((int64_t)sizeof(double) * nb * nacc * Jp, 256);
@@ -424,14 +480,16 @@ ot_status ot_assoc_shard_sweep(ot_assoc_ctx* ctx, int mode, const float* C, int6
     A.part = (double*)ws;
     A.epart = (double*)(ws + off_e);
     A.f_out = mode == OT_SHARD_FINAL ? f_out : nullptr;
+    A.state = state;
     cudaStream_t s = (cudaStream_t)stream;
     void* args[] = {&A};
     e = cudaLaunchKernel(fn, dim3(nb), dim3(SH_NW * 32), args, smem, s);
     if (e != cudaSuccess) return cuda_error(ctx, e, "shard sweep");
     const int n = nacc * (int)J;
-    k_shard_reduce<<<(n + 255) / 256, 256, 0, s>>>(A.part, A.epart, nb, nacc, Jp, (int)J,
+    k_shard_reduce<<<(n + 31) / 32, SR_WARPS * 32, 0, s>>>(A.part, A.epart, nb, nacc, Jp, (int)J,
                                                    mode == OT_SHARD_COLMAX ? 1 : 0, col_out,
-                                                   (mode == OT_SHARD_ITER || mode == OT_SHARD_FINAL) ? row_out : nullptr);
+                                                   (mode == OT_SHARD_ITER || mode == OT_SHARD_FINAL) ? row_out : nullptr,
+                                                   state);
     ctx->launches += 2;
     e = cudaGetLastError();
     return e == cudaSuccess ? OT_OK : cuda_error(ctx, e, "shard reduce");
@@ -439,7 +497,8 @@ ot_status ot_assoc_shard_sweep(ot_assoc_ctx* ctx, int mode, const float* C, int6
 
 ot_status ot_assoc_shard_update(ot_assoc_ctx* ctx, int mode, const float* q, int64_t J, double inv_qmass,
                                 const double* col, const double* colmax, const double* G_in, double* G_out,
-                                int32_t* flag, void* stream) {
+                                int32_t* flag, const double* err, int32_t iter, double tol_stop, int32_t max_iter,
+                                double* state, void* stream) {
     if (!ctx) return OT_EINVAL;
     DeviceGuardLite guard(ctx->device);
     if (mode != OT_SHARD_FIRST && mode != OT_SHARD_ITER && mode != OT_SHARD_COLSUM)
@@ -448,8 +507,10 @@ ot_status ot_assoc_shard_update(ot_assoc_ctx* ctx, int mode, const float* q, int
     if (mode == OT_SHARD_COLSUM && !colmax) return set_error(ctx, OT_EINVAL, "colmax is required");
     if (J <= 0 || J > 8192) return set_error(ctx, OT_EINVAL, "bad J");
     if (!(inv_qmass > 0.0) || !std::isfinite(inv_qmass)) return set_error(ctx, OT_EINVAL, "inv_qmass");
-    k_shard_update<<<(int)((J + 255) / 256), 256, 0, (cudaStream_t)stream>>>(mode, q, (int)J, inv_qmass, col, colmax,
-                                                                            G_in, G_out, flag);
+    if (state && mode == OT_SHARD_ITER && (!err || iter < 2 || max_iter < 1 || !(tol_stop >= 0.0)))
+        return set_error(ctx, OT_EINVAL, "a loop state needs err, iter >= 2, max_iter >= 1 and tol_stop >= 0");
+    k_shard_update<<<(int)((J + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        mode, q, (int)J, inv_qmass, col, colmax, G_in, G_out, flag, err, (int)iter, tol_stop, (int)max_iter, state);
     ctx->launches += 1;
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? OT_OK : cuda_error(ctx, e, "shard update");

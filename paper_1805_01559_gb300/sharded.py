@@ -26,6 +26,7 @@ import torch
 from . import binding as B
 
 STOP_MARGIN = 1.0 - 2.0 ** -5  # stop at residual <= tol (1 - 2^-5), as the single-GPU solver
+AHEAD = 8  # iterations enqueued between two reads of the loop state
 LOG2E = 1.0 / math.log(2.0)
 
 
@@ -65,12 +66,15 @@ class DeviceOps:
     def mass(self, p, q, out):
         self.ctx.shard_mass(p, q, out, stream=self.stream)
 
-    def sweep(self, mode, C, p, inv_mass, eps, G, F_in, F_out, colmax, col_out, row_out=None, f_out=None):
-        self.ctx.shard_sweep(mode, C, p, inv_mass, eps, G, F_in, F_out, colmax, col_out, row_out, f_out,
+    def sweep(self, mode, C, p, inv_mass, eps, G, F_in, F_out, colmax, col_out, row_out=None, f_out=None,
+              state=None):
+        self.ctx.shard_sweep(mode, C, p, inv_mass, eps, G, F_in, F_out, colmax, col_out, row_out, f_out, state,
                              stream=self.stream)
 
-    def update(self, mode, q, inv_qmass, col, colmax, G_in, G_out, flag):
-        self.ctx.shard_update(mode, q, inv_qmass, col, colmax, G_in, G_out, flag, stream=self.stream)
+    def update(self, mode, q, inv_qmass, col, colmax, G_in, G_out, flag, err=None, it=0, tol_stop=0.0,
+               max_iter=0, state=None):
+        self.ctx.shard_update(mode, q, inv_qmass, col, colmax, G_in, G_out, flag, err, it, tol_stop, max_iter,
+                              state, stream=self.stream)
 
     def finish(self, col2, row_err, q, mass, inv_qmass, eps, G, g_out, rho_out, summary):
         self.ctx.shard_finish(col2, row_err, q, mass, inv_qmass, eps, G, g_out, rho_out, summary,
@@ -103,6 +107,8 @@ class LocalReduce:
 
 
 def _combine(parts: Sequence[torch.Tensor], how: str) -> torch.Tensor:
+    if len(parts) == 1:
+        return parts[0]
     out = parts[0].clone()
     for t in parts[1:]:
         if how == "sum":
@@ -186,25 +192,30 @@ def solve_sharded(ops, shards: Sequence[Tuple[torch.Tensor, torch.Tensor]], q: t
     G = G1
 
     # ---- iterations 2, 3, ...: sweep, one sum of J + 1 doubles, column update ----------------
+    # The loop test runs in the update (a loop state on the device), so iterations are
+    # enqueued AHEAD at a time and the host reads the state once per batch; launches after
+    # the stop do nothing.  The collective still runs every enqueued iteration on every rank.
+    state = torch.zeros(4, **f64)
+    vbuf = [torch.empty(J + 1, **f64) for _ in shards]
     s = 2
     while True:
-        old, new = (s - 1) & 1, s & 1
-        parts = []
-        for (C, p), Fk in zip(shards, F):
-            v = torch.empty(J + 1, **f64)
-            ops.sweep(B.OT_SHARD_ITER, C, p, inv_mass, eps, G, Fk[old], Fk[new], None, v[:J], v[J:])
-            parts.append(v)
-        vec = _combine(parts, "sum")
-        reduce.sum(vec)
-        err, fl = float(vec[J].cpu()), int(flag.cpu()[0])  # one wait an iteration
-        if fl or not math.isfinite(err):
-            raise FloatingPointError("a column sum is not positive and finite")
-        conv = err <= tol * STOP_MARGIN
-        if conv or s - 1 >= max_iter:
-            iters, ans = s - 1, old
+        for _ in range(AHEAD):
+            old, new = (s - 1) & 1, s & 1
+            for (C, p), Fk, v in zip(shards, F, vbuf):
+                ops.sweep(B.OT_SHARD_ITER, C, p, inv_mass, eps, G, Fk[old], Fk[new], None, v[:J], v[J:], None,
+                          state)
+            vec = _combine(vbuf, "sum")
+            reduce.sum(vec)
+            ops.update(B.OT_SHARD_ITER, q, inv_qmass, vec[:J], None, G, G, flag, vec[J:], s, tol * STOP_MARGIN,
+                       max_iter, state)
+            s += 1
+        st = torch.cat([state, flag.to(torch.float64)]).cpu()
+        if st[0] != 0.0 or st[4] != 0.0:
             break
-        ops.update(B.OT_SHARD_ITER, q, inv_qmass, vec[:J], None, G, G, flag)
-        s += 1
+    reason, iters, ans, err = int(st[0]), int(st[1]), int(st[2]), float(st[3])
+    if reason == 3 or st[4] != 0.0:
+        raise FloatingPointError("a column sum is not positive and finite")
+    conv = reason == 1
 
     # ---- finalize on the returned plan (F'^iters, G^iters) -------------------------------------
     parts, fs = [], []

@@ -33,7 +33,10 @@ class NumpyOps:
         bad = not (np.isfinite(pn).all() and (pn > 0).all() and np.isfinite(qn).all() and (qn > 0).all())
         out[0], out[1], out[2] = float(pn.sum()), float(qn.sum()), 1.0 if bad else 0.0
 
-    def sweep(self, mode, C, p, inv_mass, eps, G, F_in, F_out, colmax, col_out, row_out=None, f_out=None):
+    def sweep(self, mode, C, p, inv_mass, eps, G, F_in, F_out, colmax, col_out, row_out=None, f_out=None,
+              state=None):
+        if state is not None and state[0] != 0.0:
+            return
         k = 1.0 / (eps * LN2)  # log2(e) / eps
         Cn, Gn, pn = C.numpy().astype(np.float64), G.numpy(), p.numpy().astype(np.float64)
         ph = pn * inv_mass
@@ -65,7 +68,17 @@ class NumpyOps:
             if f_out is not None:
                 f_out.numpy()[:] = eps * LN2 * (F + np.log2(pn))
 
-    def update(self, mode, q, inv_qmass, col, colmax, G_in, G_out, flag):
+    def update(self, mode, q, inv_qmass, col, colmax, G_in, G_out, flag, err=None, it=0, tol_stop=0.0,
+               max_iter=0, state=None):
+        if state is not None:
+            if state[0] != 0.0:
+                return
+            if mode == ITER:
+                e = float(err[0])
+                if not math.isfinite(e) or e <= tol_stop or it - 1 >= max_iter:
+                    state[1], state[2], state[3] = it - 1, (it - 1) & 1, e
+                    state[0] = 3.0 if not math.isfinite(e) else (1.0 if e <= tol_stop else 2.0)
+                    return
         lq = np.log2(q.numpy().astype(np.float64) * inv_qmass)
         c, g = col.numpy(), G_in.numpy().copy()
         if mode == FIRST:
@@ -77,6 +90,8 @@ class NumpyOps:
         M = colmax.numpy() if mode == COLSUM else 0.0
         if not (np.isfinite(c).all() and (c > 0).all()):
             flag[0] |= 2
+            if state is not None:
+                state[0] = 3.0
             return
         G_out.numpy()[:] = g + lq - (M + np.log2(c))
 
