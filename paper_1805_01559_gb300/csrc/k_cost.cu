@@ -31,15 +31,17 @@ static constexpr int NTC = 256;
 // as error-free FP32 pairs (no FP64: GB300 issues it at a small fraction of the FP32 rate).  Each own term P_j G_ij is kept as an exact hi + lo pair, so
 // T_i - own loses nothing when one RRH dominates (T_hi - own_hi is exact by Sterbenz).
 // ------------------------------------------------------------------------------------------
-// With C non-null the same pass also writes the cost C_ij = (1/mu) / R_ij (one IEEE FP32
-// division, as k_cost) and counts rates that are not finite and > 0; R may then be null.
+// Two passes: k_rowtot forms T_i per row (a team per row, the compensated sum above), then
+// k_rate_cells forms every cell's rate (and with C non-null the cost C_ij = (1/mu) / R_ij, one
+// IEEE FP32 division, as k_cost, counting rates that are not finite and > 0; R may then be
+// null) with one thread per 4-column chunk.  The cells' arithmetic (a division, log1pf and
+// a correctly rounded reciprocal: about 65 instructions a cell) needs more warps than a
+// team-per-row kernel at 128 registers keeps; the second read of G costs less than that
+// (the single pass ran at 249 us on 50,000 x 800).
 template <int TW, int VPT>
-__global__ void __launch_bounds__(NTC, 2) k_rates(const float* __restrict__ G, int64_t ld_g,
-                                               const float* __restrict__ P, int64_t I, int J,
-                                               float2 N0, float w_log2e, float* __restrict__ R,
-                                               int64_t ld_r, int vec_out, float inv_mu, float* __restrict__ C,
-                                               int64_t ld_c, int vec_c, unsigned long long* bad) {
-    unsigned long long nbad = 0;
+__global__ void __launch_bounds__(NTC, 2) k_rowtot(const float* __restrict__ G, int64_t ld_g,
+                                                const float* __restrict__ P, int64_t I, int J, float2 N0,
+                                                float2* __restrict__ T_out) {
     constexpr int TT = 32 * TW, NTEAMS = NTC / TT;
     constexpr int JMAX = 4 * TT * VPT;  // columns a team covers
     __shared__ float2 red[2 * NTEAMS * TW];
@@ -77,49 +79,71 @@ __global__ void __launch_bounds__(NTC, 2) k_rates(const float* __restrict__ G, i
             for (int w = 1; w < TW; ++w) T = df_add2(T, r[w]);
             par ^= 1;
         }
-        T = df_add2(T, N0);
-        const float T_hi = T.x;
-        const float T_lo = T.y;
+        if (tm.tl == 0) T_out[i] = df_add2(T, N0);
+    }
+}
+
+// One thread per (row, 4-column chunk) of a block's rows [blockIdx.x * rows, + rows).
+__global__ void __launch_bounds__(NTC) k_rate_cells(const float* __restrict__ G, int64_t ld_g,
+                                                    const float* __restrict__ P, int64_t I, int J, int rows,
+                                                    const float2* __restrict__ T, float w_log2e,
+                                                    float* __restrict__ R, int64_t ld_r, int vec_out, float inv_mu,
+                                                    float* __restrict__ C, int64_t ld_c, int vec_c,
+                                                    unsigned long long* bad) {
+    unsigned long long nbad = 0;
+    const int J4 = (J + 3) >> 2;
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int nrow = (int)min((int64_t)rows, I - r0);
+    const int n = nrow * J4;
+    for (int f = threadIdx.x; f < n; f += blockDim.x) {
+        const int rr = f / J4, c4 = f - rr * J4;
+        const int64_t i = r0 + rr;
+        const int col = 4 * c4;
+        // rows are 16-byte aligned, so a chunk that starts below J stays inside the padded row
+        float4 x = __ldg(reinterpret_cast<const float4*>(G + i * ld_g + col));
+        float4 pw;
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            const int col = 4 * (tm.tl + TT * v);
-            float4 pw = *reinterpret_cast<const float4*>(pws + col);
-            float4 r;
+        for (int c = 0; c < 4; ++c) {
+            const bool in = col + c < J;
+            if (!in) comp(x, c) = 0.0f;
+            comp(pw, c) = in ? __ldg(P + col + c) : 0.0f;
+        }
+        const float2 Ti = T[i];
+        float4 r;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            // the own term as the same exact pair as in the row total
+            const float own = comp(pw, c) * comp(x, c);
+            const float own_lo = fmaf(comp(pw, c), comp(x, c), -own);
+            const float interf = (Ti.x - own) + (Ti.y - own_lo);
+            const float sinr = interf > 0.f ? own / interf : INFINITY;
+            comp(r, c) = w_log2e * log1pf(sinr);
+        }
+        if (R) {
+            float* rrow = R + i * ld_r;
+            if (col + 4 <= J && vec_out) {
+                *reinterpret_cast<float4*>(rrow + col) = r;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (col + c < J) rrow[col + c] = comp(r, c);
+            }
+        }
+        if (C) {
+            float4 o;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                // the own term as the same exact pair as in the row total
-                const float own = comp(pw, c) * comp(x[v], c);
-                const float own_lo = fmaf(comp(pw, c), comp(x[v], c), -own);
-                const float interf = (T_hi - own) + (T_lo - own_lo);
-                const float sinr = interf > 0.f ? own / interf : INFINITY;
-                comp(r, c) = w_log2e * log1pf(sinr);
+                const float rv = comp(r, c);
+                nbad += (col + c < J) && !(rv > 0.0f && isfinite(rv));
+                comp(o, c) = __fdiv_rn(inv_mu, rv);
             }
-            if (R) {
-                float* rrow = R + i * ld_r;
-                if (col + 4 <= J && vec_out) {
-                    *reinterpret_cast<float4*>(rrow + col) = r;
-                } else {
+            float* crow = C + i * ld_c;
+            if (col + 4 <= J && vec_c) {
+                *reinterpret_cast<float4*>(crow + col) = o;
+            } else {
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (col + c < J) rrow[col + c] = comp(r, c);
-                }
-            }
-            if (C) {
-                float4 o;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float rv = comp(r, c);
-                    nbad += (col + c < J) && !(rv > 0.0f && isfinite(rv));
-                    comp(o, c) = __fdiv_rn(inv_mu, rv);
-                }
-                float* crow = C + i * ld_c;
-                if (col + 4 <= J && vec_c) {
-                    *reinterpret_cast<float4*>(crow + col) = o;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (col + c < J) crow[col + c] = comp(o, c);
-                }
+                for (int c = 0; c < 4; ++c)
+                    if (col + c < J) crow[col + c] = comp(o, c);
             }
         }
     }
@@ -139,9 +163,16 @@ ot_status launch_rates(ot_assoc_ctx* ctx, const float* G, int64_t ld_g, const fl
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((I + nteams - 1) / nteams, 8LL * ctx->num_sms));
     const float n0_hi = (float)N0;
     const float2 n0 = make_float2(n0_hi, (float)(N0 - (double)n0_hi));
-    OTA_ROW_DISPATCH(J, k_rates, <<<grid, NTC, 0, s>>>(G, ld_g, P, I, J, n0, w_log2e, R, ld_r, vec_out, inv_mu, C,
-                                                       ld_c, vec_c, bad_dev));
-    ctx->launches += 1;
+    ot_status st = OT_OK;
+    float2* T = (float2*)scratch(ctx, SLOT_ROWTOT, sizeof(float2) * (size_t)I, &st);
+    if (st) return st;
+    OTA_ROW_DISPATCH(J, k_rowtot, <<<grid, NTC, 0, s>>>(G, ld_g, P, I, J, n0, T));
+    const int J4 = (J + 3) / 4;
+    const int rows = std::max(1, 8 * NTC / J4);  // about 8 chunks a thread
+    const int64_t nblk = (I + rows - 1) / rows;
+    k_rate_cells<<<(unsigned)nblk, NTC, 0, s>>>(G, ld_g, P, I, J, rows, T, w_log2e, R, ld_r, vec_out, inv_mu, C, ld_c,
+                                                vec_c, bad_dev);
+    ctx->launches += 2;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(ctx, e, "rates launch");
     return OT_OK;

@@ -29,6 +29,7 @@ enum ScratchSlot {
     SLOT_ALIGN,        // 16-byte-aligned copies of unaligned caller inputs (G, R)
     SLOT_TUNE,         // autotuner outputs (potentials of the timed runs)
     SLOT_SHARD,        // row-sharded sweeps: per-block column partials
+    SLOT_ROWTOT,       // rates: per-row totals N0 + sum_k P_k G_ik (FP32 pairs)
     SLOT_COUNT
 };
 
