@@ -39,7 +39,7 @@ static constexpr int NTC = 256;
 // team-per-row kernel at 128 registers keeps; the second read of G costs less than that
 // (the single pass ran at 249 us on 50,000 x 800).
 template <int TW, int VPT>
-__global__ void __launch_bounds__(NTC, 2) k_rowtot(const float* __restrict__ G, int64_t ld_g,
+__global__ void __launch_bounds__(NTC, 4) k_rowtot(const float* __restrict__ G, int64_t ld_g,
                                                 const float* __restrict__ P, int64_t I, int J, float2 N0,
                                                 float2* __restrict__ T_out) {
     constexpr int TT = 32 * TW, NTEAMS = NTC / TT;
