@@ -291,6 +291,9 @@ def run_reference(args):
     return 0
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal: stated beside the measured copy bandwidth
+
+
 def solve_roofline(per_launch, I: int, J: int, peak: float):
     """Roofline of the solver over a step's launches.
 
@@ -485,6 +488,8 @@ def run_gpu(args):
                                        "their summed kernel time (CUDA events on the solve stream)",
                          "alg_bytes_per_launch": roof["alg_bytes_per_launch"],
                          "frac_incl_setup_finalize": roof["frac_incl_setup_finalize"],
+                         "nominal_peak": NOMINAL_HBM_GBS,
+                         "frac_of_nominal": (roof["achieved"] / NOMINAL_HBM_GBS) if roof["achieved"] else None,
                          "reads_of_C_per_launch": "iters + 2" if not args.multi else
                          "iters + 2, then max(iters) + 2 x 2",
                          "per_launch": roof["per_launch"],
@@ -494,6 +499,16 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clk,
         }
+        if ws == 1:
+            # the per-cell exponential against the SFU's measured ceiling: one ex2 a cell and
+            # sweep, iters + 2 sweeps a launch
+            rate = ctx.measure_ex2_rate()
+            ls = [x for lst in per_launch for x in lst]
+            if ls and rate > 0:
+                need = sum(float(I) * J * (x[1] + 2) for x in ls) / (sum(x[0] for x in ls) / 1e3)
+                line["sfu"] = {"ex2_per_s_measured": rate, "solver_ex2_per_s": need, "frac": need / rate,
+                               "definition": "ex2 results/s of ot_assoc_measure_ex2_rate (8 independent chains a "
+                                             "thread) against I x J x (iters + 2) / sk_solve time"}
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(inst)
         if ws == 1 and args.sub_records:
@@ -1279,6 +1294,75 @@ def run_sharded(args):
     return 0
 
 
+def run_oracle(args):
+    """The FP64 oracle's own speed on the host cores, all of them and one (CPU only; run on the
+    GPU machine's host so that the numbers describe the cores beside the GPU): the 1000 x 50
+    instance solved to tol; the 50,000 x 800 step's instance at eps = 0.1 median(C), to tol on
+    all cores and 2 iterations on one; a 20,000 x 512 sample of the 400,000 x 4,096
+    configuration, to tol on all cores and 20 iterations on one; the whole 400,000 x 4,096
+    instance, 2 iterations on all cores (its eps from a 1% row sample of C: only the timing
+    matters).  Bounded so that the run takes a few minutes."""
+    import oracle
+    from paper_1805_01559_gb300 import instances as ins
+    nall = oracle.num_threads()
+
+    def solve(C, p, q, eps, tol, iters, threads):
+        oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        _, _, it, _ = oracle.sinkhorn(C, p, q, eps, tol, iters)
+        dt = time.perf_counter() - t0
+        return {"threads": threads, "iters": int(it), "tol": tol, "s": dt,
+                "cells_iters_per_s": float(C.shape[0]) * C.shape[1] * it / dt}
+
+    def cost64(G, P, N0, W, mu):
+        return oracle.cost(oracle.rates(np.asarray(G, np.float64), P, N0, W), mu)
+
+    res = {}
+    inst = ins.config1()
+    C = cost64(inst.G, inst.P, inst.N0, inst.W_hz, inst.mu)
+    eps = inst.eps_rel[0] * oracle.median(C)
+    res["c1_1000x50"] = [solve(C, inst.lam, inst.q, eps, TOL, MAX_ITER, n) for n in (nall, 1)]
+    inst = make_inputs()
+    C = cost64(inst.G, inst.P, inst.N0, inst.W_hz, inst.mu)
+    eps = 0.1 * oracle.median(C)
+    res["c2_50000x800_eps0.1"] = [solve(C, inst.lam, inst.q, eps, TOL, MAX_ITER, nall),
+                                  solve(C, inst.lam, inst.q, eps, 0.0, 2, 1)]
+    inst = ins.make_instance("c4_sub", 20000, 512, 4000.0 * np.sqrt(20000 / 400000), 4, hotspot=True,
+                             traffic_sigma=1.5, marginal="capacity", dtype=np.float32)
+    C = cost64(inst.G, inst.P, inst.N0, inst.W_hz, inst.mu)
+    eps = 0.05 * oracle.median(C)
+    res["c4_sample_20000x512"] = [solve(C, inst.lam, inst.q, eps, TOL, MAX_ITER, nall),
+                                  solve(C, inst.lam, inst.q, eps, 0.0, 20, 1)]
+    del C
+    I, J, block = args.c4_rows, 4096, 8192
+    inst = ins.config4_blocked(0, I, J, block)
+    C = np.empty((I, J), np.float64)
+    oracle.set_threads(nall)
+    t0 = time.perf_counter()
+    pool = _pool(min(16, os.cpu_count() or 1))
+    try:
+        for b, G in pool.imap_unordered(_gen_c4_block, [(0, I, J, block, b) for b in range(inst.nblocks)]):
+            C[b * block:b * block + G.shape[0]] = oracle.cost(oracle.rates_total(G, inst.P, inst.N0, inst.W_hz),
+                                                              inst.mu)
+    finally:
+        pool.close()
+    gen_s = time.perf_counter() - t0
+    eps = 0.05 * oracle.median(C[::100])
+    res[f"c4_{I}x{J}"] = [solve(C, inst.lam, inst.q, eps, 0.0, 2, nall)]
+    del C
+    oracle.set_threads(nall)
+    c2 = res["c2_50000x800_eps0.1"][0]
+    line = {"metric": "oracle cells*iters/s", "value": c2["cells_iters_per_s"], "unit": "cells*iters/s",
+            "n_gpus": 0, "steps": 1, "warmup": 0, "ms_per_step": c2["s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "oracle timing: c1, the 50,000 x 800 step's first eps, a 20,000 x 512 sample "
+                                   "and the whole 400,000 x 4,096 instance; all host cores and one",
+                       "cores": nall, "c4_inputs_s": gen_s},
+            "oracle_timing": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_epsscale(args):
     """eps-scaling on the 50,000 x 800 step's instance: Algorithm 1 at eps = e x median(C)
     from b = 1 (sk_solve) against the same eps reached through the stages 0.1 -> 0.03 -> ...
@@ -1361,7 +1445,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=12_500)
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="only run this many rounds of the three solves of one step (for profiler captures)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2", "policies", "euclid", "epsscale", "sharded"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "alg2", "policies", "euclid", "epsscale", "sharded", "oracle"],
                     help="c2: the headline line; c3 batched ragged; c4 stored-kernel precision; c5 serving; "
                          "alg2 adaptive association (Algorithm 2)")
     ap.add_argument("--alg2-outer", type=int, default=20)
@@ -1386,7 +1470,7 @@ def main():
     if args.workload != "c2" and args.impl != "reference":
         return {"c3": run_c3, "c4": run_c4, "c5": run_c5, "alg2": run_alg2,
                 "policies": run_policies, "euclid": run_euclid, "epsscale": run_epsscale,
-                "sharded": run_sharded}[args.workload](args)
+                "sharded": run_sharded, "oracle": run_oracle}[args.workload](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

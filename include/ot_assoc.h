@@ -477,6 +477,12 @@ ot_status ot_assoc_solve_eps_scaling(ot_assoc_ctx* ctx, const float* C, int64_t 
                                      int32_t warm_start, ot_assoc_result* out, int32_t* stage_iters,
                                      int32_t* nstages_out, void* stream);
 
+/* Measurement: the FP32 exp2 throughput of ctx's device (the SFU, one ex2.approx a cell and
+ * sweep in every Algorithm 1 solver here), from 8 independent exp2 chains a thread over
+ * 8 blocks of 256 threads an SM, timed with events (best of 3 after a warm-up launch).
+ * *ex2_per_s [host].  Synchronises `stream`; a few ms. */
+ot_status ot_assoc_measure_ex2_rate(ot_assoc_ctx* ctx, double* ex2_per_s, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * Row-sharded Algorithm 1 (Sec. III-C, Eqs. (3)-(5)): the rows of C split into contiguous
  * shards (one per rank / GPU).  The row update (Eq. (3)) only needs a shard's own rows; the

@@ -1134,3 +1134,20 @@ Context.shard_mass = _ctx_shard_mass
 Context.shard_sweep = _ctx_shard_sweep
 Context.shard_update = _ctx_shard_update
 Context.shard_finish = _ctx_shard_finish
+
+
+# ---- measurement: the SFU exp2 throughput ------------------------------------------------------
+SIGNATURES["ot_assoc_measure_ex2_rate"] = (ctypes.c_int, [_VP, _PD, _VP])
+if _lib is not None:
+    _lib.ot_assoc_measure_ex2_rate.restype, _lib.ot_assoc_measure_ex2_rate.argtypes = \
+        SIGNATURES["ot_assoc_measure_ex2_rate"]
+
+
+def _ctx_measure_ex2_rate(self, stream=None) -> float:
+    """FP32 exp2 results per second of the device (the per-cell exponential's ceiling)."""
+    out = ctypes.c_double(0.0)
+    self._check(self._L.ot_assoc_measure_ex2_rate(self._h, ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+Context.measure_ex2_rate = _ctx_measure_ex2_rate
