@@ -226,3 +226,21 @@ def test_two_gloo_ranks_converge_like_the_oracle():
     cost, _, er, ec = oracle.finalize(C.astype(np.float64), f, got[0][2], p, q, eps)
     assert er <= tol and ec <= tol
     assert got[0][4] == pytest.approx(cost, rel=1e-12)
+
+
+def test_a_column_without_links_fails_loudly():
+    # column 0 has no finite cost: its sum is 0 in iteration 1, the exact passes cannot repair
+    # it, and the driver raises instead of returning potentials
+    C, p, q = _instance(17, 120, 9)
+    C[:, 0] = np.inf
+    with np.errstate(all="ignore"), pytest.raises(FloatingPointError):
+        S.solve_sharded(NumpyOps(), _shards(C, p, [60]), torch.from_numpy(q), 0.1, tol=1e-6, max_iter=50)
+
+
+def test_max_iter_one_returns_the_first_iterate():
+    C, p, q = _instance(19, 150, 11)
+    res = S.solve_sharded(NumpyOps(), _shards(C, p, [70]), torch.from_numpy(q), 0.2, tol=1e-9, max_iter=1)
+    f_or, g_or, it_or, err_or = oracle.sinkhorn(C.astype(np.float64), p, q, 0.2, 0.0, 1)
+    assert res.iters == 1 and not res.converged
+    assert res.err_loop == pytest.approx(err_or, rel=1e-9)
+    _plan_close(C, np.concatenate([t.numpy() for t in res.f]), res.g.numpy(), f_or, g_or, 0.2, 1e-9)
