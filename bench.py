@@ -1194,17 +1194,19 @@ def run_euclid(args):
     ms = statistics.median(ms_f)
     ci = float(I) * J * sum(its)
     # two SFU operations a cell and sweep (the exponential and the square root's reciprocal
-    # square root): 152 SMs x 16 SFU results a clock x 2.07 GHz / 2; and the issue bound of
-    # the kernel's instruction mix: 152 SMs x 4 schedulers x 1 warp instruction a clock x
+    # square root) against the device's measured exp2 rate; and the issue bound of the
+    # kernel's instruction mix: 152 SMs x 4 schedulers x 1 warp instruction a clock x
     # 2.07 GHz / (warp instructions per cell and sweep, counted by ncu).  The lower binds.
-    sfu_cells = 152 * 16 * 2.07e9 / 2
+    ex2_rate = ctx.measure_ex2_rate()
+    sfu_cells = ex2_rate / 2
     wi = stored_euclid_inst()
     issue_cells = 152 * 4 * 2.07e9 / wi if wi else None
     if issue_cells and issue_cells < sfu_cells:
         peak_cells, peak_kind = issue_cells, (f"derived: issue bound, 152 SMs x 4 warp instructions/clk x 2.07 GHz / "
                                               f"{wi:.4f} warp instructions per cell and sweep (ncu count)")
     else:
-        peak_cells, peak_kind = sfu_cells, "derived: 152 SMs x 16 SFU/clk x 2.07 GHz / 2 SFU ops per cell"
+        peak_cells, peak_kind = sfu_cells, (f"measured: {ex2_rate:.3g} exp2/s (ot_assoc_measure_ex2_rate) / 2 SFU "
+                                            "ops per cell")
     sweeps = sum(it + 2 for it in its)
     achieved = float(I) * J * sweeps / (ms / 1e3)
     line = {"metric": METRIC, "value": ci / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
